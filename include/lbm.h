@@ -1,0 +1,163 @@
+/*
+ * lbm.h -- C interface of liblbm.so: one explicit time step of the 2-D
+ * 16-velocity (Kataoka-Tsutahara) multiple-relaxation-time finite-difference
+ * lattice Boltzmann model with flux-limited convection (Chen, Xu, Zhang, Wang,
+ * arXiv:1305.4736), on an NVIDIA GB300 (sm_103a).
+ *
+ * General conventions
+ *  - Every call returns LBM_OK (0) or a negative LBM_ERR_* code; no C++
+ *    exception crosses this interface.  lbm_last_error() describes the last
+ *    failure of a context (or of this thread when the context is NULL).
+ *  - Host arrays are caller-owned, row-major [ny][nx] float64 (fields) or
+ *    [16][ny][nx] float64 (population / moment sets), copied in or out during
+ *    the call and never retained.
+ *  - Device memory belongs to the context: two 16-plane buffers (ping-pong) of
+ *    (ny + 4) rows by a padded pitch, allocated at create time through the
+ *    allocator given to lbm_create_ex (default: cudaMalloc) and released by
+ *    lbm_destroy.  All work is enqueued on the context's CUDA stream.
+ *  - Grid: cell-centred, dx = dy, two ghost layers on every edge.  R = 1, so
+ *    the pressure is P = rho T.  gamma = (b + 2)/b (Sec. II).
+ *  - Relaxation rates s[0..15] are s_1 .. s_16 of Eq. (3); s_1..s_4 belong to
+ *    conserved moments and are ignored.
+ *  - Populations are ordered: i = 0..3 (1,0),(0,1),(-1,0),(0,-1); i = 4..7 the
+ *    same times 6; i = 8..11 sqrt2 (1,1),(-1,1),(-1,-1),(1,-1); i = 12..15
+ *    (3/sqrt2) (1,1),(-1,1),(-1,-1),(1,-1).  Moment rows k = 0..15 are
+ *    m_1 .. m_16 of Appendix A.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,        /* invalid argument (NULL, sizes, rates, BC pairing) */
+    LBM_ERR_CFL = -2,        /* max_i,a |v_ia| dt/dx > 1 (Sec. III update would be unstable) */
+    LBM_ERR_STABILITY = -3,  /* some s_k dt >= 2 (k >= 5): forward-Euler relaxation unstable */
+    LBM_ERR_OOM = -4,        /* device allocation failed */
+    LBM_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error, ...) */
+    LBM_ERR_NONFINITE = -6,  /* a moment read-back found a non-finite value or rho <= 0 */
+    LBM_ERR_STATE = -7,      /* call out of order (step before init, n <= 0, ...) */
+    LBM_ERR_TIMEOUT = -8     /* reserved: a bounded device wait ran out */
+};
+
+/* Convection schemes of Sec. III. */
+enum {
+    LBM_LIMITER_MC = 0,      /* the paper's flux limiter psi(theta) (monotonised central) */
+    LBM_LIMITER_LW = 1,      /* psi = 1: Lax-Wendroff */
+    LBM_LIMITER_UPWIND = 2   /* psi = 0: first-order upwind */
+};
+
+/* Ghost-cell kinds (Sec. IV.A periodic / fixed equilibrium, Sec. IV.C
+   non-equilibrium extrapolation wall, Sec. V inflow / outflow). */
+enum {
+    LBM_BC_PERIODIC = 0,       /* copy from the opposite edge; must be set on both edges of an axis */
+    LBM_BC_ZERO_GRADIENT = 1,  /* copy the nearest interior cell (outflow) */
+    LBM_BC_EQUILIBRIUM = 2,    /* f = M^-1 f_hat^eq(rho, u, v, T) of the edge state (inflow) */
+    LBM_BC_NEQ_WALL = 3        /* wall on the face with velocity (u, v) and temperature T:
+                                  ghost g, mirror m (-1<->0, -2<->1): rho_g = rho_m,
+                                  u_g = 2 u_w - u_m, T_g = 2 T_w - T_m,
+                                  f_g = f^eq(g) + (f_m - f^eq(m)); rho is unused */
+};
+
+/* Storage / arithmetic precision. */
+enum {
+    LBM_FP64 = 0,      /* f stored and updated in float64 */
+    LBM_FP32_DEV = 1   /* g = f - f^eq(rho0, 0, 0, T0) stored and updated in float32;
+                          moments recovered in float64 */
+};
+
+typedef struct { int kind; double rho, u, v, T; } lbm_edge_bc;
+typedef struct { lbm_edge_bc xlo, xhi, ylo, yhi; } lbm_bc;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+   alloc returns a device pointer of at least `bytes` bytes usable on `stream`
+   (NULL on failure); free releases it.  Both are called only from
+   lbm_create_ex (alloc) and lbm_destroy (free), on the calling thread. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} lbm_allocator;
+
+/* Extended options of lbm_create_ex. */
+typedef struct {
+    int precision;                 /* LBM_FP64 or LBM_FP32_DEV */
+    double rho0, T0;               /* reference state of LBM_FP32_DEV (default 1, 1 when <= 0) */
+    void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
+    const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
+    int device;                    /* CUDA device ordinal; < 0 = the current device */
+} lbm_options;
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
+
+/* Create a problem: grid nx x ny (>= 1), spacing dx (= dy) > 0, time step dt > 0,
+   gamma > 1, Prandtl number Pr > 0, rates s[16], limiter, boundary kinds.
+   s[7] (s_8) <= 0 means s_8 = s_9 = Pr s_5; otherwise |s_8/s_5 - Pr| must be <= 1e-12 Pr.
+   Isotropy s_5 = s_6 = s_7 and s_8 = s_9 is required (Sec. II).
+   Errors: LBM_ERR_ARG, LBM_ERR_CFL, LBM_ERR_STABILITY, LBM_ERR_OOM, LBM_ERR_CUDA.
+   On success *out receives the context (FP64, legacy default stream, cudaMalloc). */
+int lbm_create(int nx, int ny, double dx, double dt, double gamma, double Pr,
+               const double s[16], int limiter, const lbm_bc *bc, lbm_ctx **out);
+
+/* As lbm_create with precision, stream, allocator and device options (opt may be NULL). */
+int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
+                  const double s[16], int limiter, const lbm_bc *bc,
+                  const lbm_options *opt, lbm_ctx **out);
+
+/* Initialise every interior cell to f = M^-1 f_hat^eq(rho, u, v, T) (Appendix A;
+   the initialisation practice of Sec. IV.A).  Host arrays [ny][nx]; rho > 0, T > 0
+   (LBM_ERR_ARG otherwise).  Synchronous. */
+int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *v, const double *T);
+
+/* Enqueue n >= 1 time steps (ghost fill + fused collide/convect per step; Eq. (3) and
+   the update of Sec. III).  Asynchronous on the context's stream.
+   LBM_ERR_STATE if n <= 0 or the context was never initialised. */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Macroscopic fields and non-equilibrium moments Delta_k = (M f)_k - f_hat^eq_k
+   (Sec. V).  Outputs [ny][nx] (rho, u, v, T) and [16][ny][nx] (delta); any output
+   may be NULL.  Synchronous.  LBM_ERR_NONFINITE if a cell has a non-finite value or
+   rho <= 0 (outputs are still written). */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, double *T, double *delta);
+
+/* Central non-equilibrium moments Delta*_k = (M* (f - f^eq))_k with M* built at each
+   cell's own flow velocity (Sec. V, Appendix A).  Output [16][ny][nx].  Synchronous. */
+int lbm_moments_central(lbm_ctx *ctx, double *delta_star);
+
+/* Domain totals of rho, j_x, j_y and e (twice the total energy), each times dx dy,
+   summed in float64 in a fixed order (deterministic).  Synchronous. */
+int lbm_totals(lbm_ctx *ctx, double out[4]);
+
+/* Interior populations f (not g, in LBM_FP32_DEV) as [16][ny][nx] float64: read / write.
+   Synchronous.  lbm_set_state also marks the context initialised. */
+int lbm_get_state(lbm_ctx *ctx, double *f);
+int lbm_set_state(lbm_ctx *ctx, const double *f);
+
+/* Interior populations of rows row0 .. row0+rows-1 only, as [16][rows][nx] float64
+   (a window of lbm_get_state, for chunked checkpoints and sampled checks).
+   LBM_ERR_ARG if the window leaves [0, ny).  Synchronous. */
+int lbm_get_state_rows(lbm_ctx *ctx, int row0, int rows, double *f);
+
+/* Steps taken since the last lbm_init / lbm_set_state. */
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Device footprint in bytes of a problem of this size and precision (both buffers). */
+size_t lbm_footprint(int nx, int ny, int precision);
+
+/* Text of the last error (never NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Release the context and its device memory (waits for its stream).  NULL-safe. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

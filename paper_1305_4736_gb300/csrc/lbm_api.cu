@@ -1,0 +1,572 @@
+// lbm_api.cu -- host side of liblbm.so: the C interface declared in include/lbm.h.
+//
+// Responsibilities: argument validation (isotropy and Prandtl number of
+// Sec. II, Courant and relaxation stability limits of the forward-Euler
+// scheme of Sec. III, boundary pairing), the constant tables of the step
+// (block inverses of the symmetry-factored transformation matrix, per-shell
+// Courant numbers, fixed-equilibrium ghost states), device memory, chunked
+// host <-> device transfers, and error reporting.  No exception crosses the
+// interface: every entry point returns a status code.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::NQ;
+using lbm::Params;
+
+struct lbm_ctx {
+    Params P;
+    int prec = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbm_allocator alloc{};
+    bool own_alloc = true;
+    void *buf = nullptr;          // both population buffers
+    size_t buf_bytes = 0;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *stage = nullptr;      // staging for chunked transfers
+    size_t stage_elems = 0;
+    double *aux = nullptr;        // totals partials (kTotalsBlocks * 4) + out (4) + flag
+    size_t aux_bytes = 0;
+    int *flag = nullptr;
+    double *tot_out = nullptr;
+    bool initialized = false;
+    long long steps = 0;
+    double dx = 0.0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(lbm_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_err = msg;
+    return code;
+}
+
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Gauss-Jordan inverse with partial pivoting (n <= 4).  Returns false if singular.
+bool invert(int n, const double *A, double *Ai)
+{
+    double a[4][8];
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < 2 * n; c++) a[r][c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; col++) {
+        int p = col;
+        for (int r = col + 1; r < n; r++)
+            if (std::fabs(a[r][col]) > std::fabs(a[p][col])) p = r;
+        if (a[p][col] == 0.0) return false;
+        if (p != col)
+            for (int c = 0; c < 2 * n; c++) std::swap(a[p][c], a[col][c]);
+        const double d = a[col][col];
+        for (int c = 0; c < 2 * n; c++) a[col][c] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == col) continue;
+            const double m = a[r][col];
+            if (m != 0.0)
+                for (int c = 0; c < 2 * n; c++) a[r][c] -= m * a[col][c];
+        }
+    }
+    for (int r = 0; r < n; r++)
+        for (int c = 0; c < n; c++) Ai[r * n + c] = a[r][n + c];
+    return true;
+}
+
+// The five blocks of the transformation matrix in the shell-butterfly basis
+// (rows of Appendix A evaluated on the velocity set of Sec. II), inverted and
+// scaled by the butterfly normalisation (axis shells: S/4, X/2, Y/2, Q/4;
+// diagonal shells: all /4).
+bool build_inverse_blocks(Params &P)
+{
+    const double r2 = lbm::kSqrt2, d3 = lbm::kD3, d4 = lbm::kD4, w1 = lbm::kW1;
+    // isotropic block: rows m1, m4, m5, m14; columns S1..S4
+    const double A[16] = {1.0, 1.0, 1.0, 1.0,
+                          w1, 36.0, 4.0, 9.0,
+                          1.0, 36.0, 4.0, 9.0,
+                          w1, 1296.0, 16.0, 81.0};
+    // x-odd block: rows m2, m8, m10, m12; columns X1..X4
+    const double E[16] = {1.0, 6.0, d3, d4,
+                          w1, 216.0, 4.0 * r2, 27.0 / r2,
+                          1.0, 216.0, 4.0 * r2, 27.0 / r2,
+                          1.0, 216.0, 0.0, 0.0};
+    double Ey[16];
+    std::memcpy(Ey, E, sizeof(E));
+    for (int c = 0; c < 4; c++) Ey[12 + c] = -E[12 + c];      // m13 = -v_y^3 on axis shells
+    const double B1[4] = {1.0, 36.0, w1, 1296.0};              // rows m6, m16; columns Q1, Q2
+    const double B2[4] = {2.0, 4.5, 8.0, 40.5};                // rows m7, m15; columns Q3, Q4
+    double Ai[16], Ei[16], Eyi[16], B1i[4], B2i[4];
+    if (!invert(4, A, Ai) || !invert(4, E, Ei) || !invert(4, Ey, Eyi) || !invert(2, B1, B1i) ||
+        !invert(2, B2, B2i))
+        return false;
+    const double nS = 0.25, nXa = 0.5, nXd = 0.25, nQ = 0.25;
+    for (int k = 0; k < 4; k++) {
+        const double nx = k < 2 ? nXa : nXd;
+        for (int j = 0; j < 4; j++) {
+            P.iA[k][j] = nS * Ai[k * 4 + j];
+            P.iEx[k][j] = nx * Ei[k * 4 + j];
+            P.iEy[k][j] = nx * Eyi[k * 4 + j];
+        }
+    }
+    for (int k = 0; k < 2; k++)
+        for (int j = 0; j < 2; j++) {
+            P.iB1[k][j] = nQ * B1i[k * 2 + j];
+            P.iB2[k][j] = nQ * B2i[k * 2 + j];
+        }
+    return true;
+}
+
+void fold_rates(Params &P, const double *s, double dt)
+{
+    // collision columns: moment row k (1-based) relaxes at s_k; dt folded in
+    for (int k = 0; k < 4; k++) {
+        P.cA[k][0] = dt * s[4] * P.iA[k][2];      // m5
+        P.cA[k][1] = dt * s[13] * P.iA[k][3];     // m14
+        P.cEx[k][0] = dt * s[7] * P.iEx[k][1];    // m8
+        P.cEx[k][1] = dt * s[9] * P.iEx[k][2];    // m10
+        P.cEx[k][2] = dt * s[11] * P.iEx[k][3];   // m12
+        P.cEy[k][0] = dt * s[8] * P.iEy[k][1];    // m9
+        P.cEy[k][1] = dt * s[10] * P.iEy[k][2];   // m11
+        P.cEy[k][2] = dt * s[12] * P.iEy[k][3];   // m13
+    }
+    for (int k = 0; k < 2; k++) {
+        P.cB1[k][0] = dt * s[5] * P.iB1[k][0];    // m6
+        P.cB1[k][1] = dt * s[15] * P.iB1[k][1];   // m16
+        P.cB2[k][0] = dt * s[6] * P.iB2[k][0];    // m7
+        P.cB2[k][1] = dt * s[14] * P.iB2[k][1];   // m15
+    }
+}
+
+// f^eq (or f^eq - f^eq0 in deviation mode) of a state, on the host.
+template <bool Dev>
+void host_feq(const Params &P, double rho, double ux, double uy, double T, double *f)
+{
+    double q[NQ];
+    lbm::feq_hat_dev<double, Dev>(P, rho - P.rho0, rho * ux, rho * uy, rho * T - P.P0, 1.0 / rho, q);
+    lbm::pop_from_moments(P, q, f);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate_bc_edge(const lbm_edge_bc &e, const char *name, std::string &msg)
+{
+    if (e.kind < LBM_BC_PERIODIC || e.kind > LBM_BC_NEQ_WALL) {
+        msg = std::string("bc ") + name + ": unknown kind";
+        return LBM_ERR_ARG;
+    }
+    if (e.kind == LBM_BC_EQUILIBRIUM &&
+        (!finite_pos(e.rho) || !finite_pos(e.T) || !std::isfinite(e.u) || !std::isfinite(e.v))) {
+        msg = std::string("bc ") + name + ": equilibrium state needs rho > 0, T > 0, finite u, v";
+        return LBM_ERR_ARG;
+    }
+    if (e.kind == LBM_BC_NEQ_WALL && (!finite_pos(e.T) || !std::isfinite(e.u) || !std::isfinite(e.v))) {
+        msg = std::string("bc ") + name + ": wall needs T > 0 and finite velocity";
+        return LBM_ERR_ARG;
+    }
+    return LBM_OK;
+}
+
+void *default_alloc(size_t bytes, void *, void *)
+{
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+void default_free(void *p, size_t, void *, void *) { cudaFree(p); }
+
+size_t pitch_of(int nx) { return (size_t)((nx + 8 + 31) / 32 * 32); }
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_footprint(int nx, int ny, int precision)
+{
+    if (nx < 1 || ny < 1) return 0;
+    const size_t es = precision == LBM_FP32_DEV ? sizeof(float) : sizeof(double);
+    return 2 * (size_t)NQ * (size_t)(ny + 4) * pitch_of(nx) * es;
+}
+
+int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr, const double s_in[16],
+                  int limiter, const lbm_bc *bc, const lbm_options *opt, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!s_in || !bc) return fail(nullptr, LBM_ERR_ARG, "s or bc is NULL");
+    if (nx < 1 || ny < 1) return fail(nullptr, LBM_ERR_ARG, "nx and ny must be >= 1");
+    if ((long long)nx * ny > (1LL << 31) - 1 || nx > (1 << 28) || ny > (1 << 28))
+        return fail(nullptr, LBM_ERR_ARG, "grid too large");
+    if (!finite_pos(dx) || !finite_pos(dt)) return fail(nullptr, LBM_ERR_ARG, "dx and dt must be finite and > 0");
+    if (!std::isfinite(gamma) || !(gamma > 1.0)) return fail(nullptr, LBM_ERR_ARG, "gamma must be > 1");
+    if (!finite_pos(Pr)) return fail(nullptr, LBM_ERR_ARG, "Pr must be finite and > 0");
+    if (limiter < LBM_LIMITER_MC || limiter > LBM_LIMITER_UPWIND) return fail(nullptr, LBM_ERR_ARG, "unknown limiter");
+    const int prec = opt ? opt->precision : LBM_FP64;
+    if (prec != LBM_FP64 && prec != LBM_FP32_DEV) return fail(nullptr, LBM_ERR_ARG, "unknown precision");
+    std::string msg;
+    const lbm_edge_bc *edges[4] = {&bc->xlo, &bc->xhi, &bc->ylo, &bc->yhi};
+    const char *names[4] = {"xlo", "xhi", "ylo", "yhi"};
+    for (int e = 0; e < 4; e++) {
+        const int rc = validate_bc_edge(*edges[e], names[e], msg);
+        if (rc) return fail(nullptr, rc, msg);
+    }
+    if ((bc->xlo.kind == LBM_BC_PERIODIC) != (bc->xhi.kind == LBM_BC_PERIODIC) ||
+        (bc->ylo.kind == LBM_BC_PERIODIC) != (bc->yhi.kind == LBM_BC_PERIODIC))
+        return fail(nullptr, LBM_ERR_ARG, "periodic boundaries must be set on both edges of an axis");
+    double s[16];
+    for (int k = 0; k < 16; k++) s[k] = s_in[k];
+    for (int k = 4; k < 16; k++)
+        if (!std::isfinite(s[k]) || s[k] < 0.0) {
+            if (k == 7 && s[k] <= 0.0) continue;
+            return fail(nullptr, LBM_ERR_ARG, "relaxation rates s_5..s_16 must be finite and >= 0");
+        }
+    if (s[7] <= 0.0) {
+        s[7] = s[8] = Pr * s[4];
+    } else {
+        if (!(s[4] > 0.0) || std::fabs(s[7] / s[4] - Pr) > 1e-12 * Pr)
+            return fail(nullptr, LBM_ERR_ARG, "Pr must equal s_8 / s_5 (Sec. II)");
+    }
+    if (s[4] != s[5] || s[4] != s[6] || s[7] != s[8])
+        return fail(nullptr, LBM_ERR_ARG, "isotropy requires s_5 = s_6 = s_7 and s_8 = s_9 (Sec. II)");
+    for (int k = 4; k < 16; k++)
+        if (s[k] * dt >= 2.0) return fail(nullptr, LBM_ERR_STABILITY, "s_k dt >= 2 for some k >= 5");
+    // largest velocity component is 6 (shell 2): Courant number 6 dt / dx
+    if (6.0 * dt / dx > 1.0) return fail(nullptr, LBM_ERR_CFL, "Courant number 6 dt/dx exceeds 1");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx;
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    Params &P = c->P;
+    std::memset(&P, 0, sizeof(P));
+    c->prec = prec;
+    c->dx = dx;
+    P.nx = nx;
+    P.ny = ny;
+    P.pitch = (int)pitch_of(nx);
+    P.plane = (long long)(ny + 4) * P.pitch;
+    P.limiter = limiter;
+    P.b = 2.0 / (gamma - 1.0);
+    P.inv_b = 1.0 / P.b;
+    P.dt = dt;
+    if (prec == LBM_FP32_DEV) {
+        P.rho0 = (opt && opt->rho0 > 0.0) ? opt->rho0 : 1.0;
+        P.T0 = (opt && opt->T0 > 0.0) ? opt->T0 : 1.0;
+        P.P0 = P.rho0 * P.T0;
+        P.e0 = P.b * P.P0;
+    }
+    if (!build_inverse_blocks(P)) {
+        delete c;
+        return fail(nullptr, LBM_ERR_ARG, "transformation blocks are singular");
+    }
+    fold_rates(P, s, dt);
+    const double k8 = (s[7] == s[4]) ? 0.0 : s[7] / s[4] - 1.0;
+    const double k9 = (s[8] == s[4]) ? 0.0 : s[8] / s[4] - 1.0;
+    P.has_c9 = (k8 != 0.0 || k9 != 0.0) ? 1 : 0;
+    P.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
+    P.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
+    // Courant number per shell: dt / (A_i dx), A_i = 1, 1/6, 1/sqrt2, sqrt2/3 (Sec. III)
+    const double A[4] = {1.0, 1.0 / 6.0, 1.0 / lbm::kSqrt2, lbm::kSqrt2 / 3.0};
+    for (int k = 0; k < 4; k++) {
+        P.cr[k] = dt / (A[k] * dx);
+        P.hh[k] = 0.25 * (1.0 - P.cr[k]);
+    }
+    if (prec == LBM_FP32_DEV) host_feq<false>(P, P.rho0, 0.0, 0.0, P.T0, P.feq0);
+    for (int e = 0; e < 4; e++) {
+        lbm::EdgeDev &E = P.edge[e];
+        E.kind = edges[e]->kind;
+        E.uw = edges[e]->u;
+        E.vw = edges[e]->v;
+        E.Tw = edges[e]->T;
+        E.dTw = edges[e]->T - P.T0;
+        if (E.kind == LBM_BC_EQUILIBRIUM) {
+            if (prec == LBM_FP32_DEV) host_feq<true>(P, edges[e]->rho, edges[e]->u, edges[e]->v, edges[e]->T, E.feq);
+            else host_feq<false>(P, edges[e]->rho, edges[e]->u, edges[e]->v, edges[e]->T, E.feq);
+        }
+    }
+
+    // device, stream, allocator
+    cudaError_t ce;
+    if (opt && opt->device >= 0) {
+        ce = cudaSetDevice(opt->device);
+        if (ce != cudaSuccess) { delete c; return cuda_fail(nullptr, ce, "cudaSetDevice"); }
+    }
+    ce = cudaGetDevice(&c->device);
+    if (ce != cudaSuccess) { delete c; return cuda_fail(nullptr, ce, "cudaGetDevice"); }
+    c->stream = opt ? (cudaStream_t)opt->stream : nullptr;
+    if (opt && opt->allocator && opt->allocator->alloc && opt->allocator->free) {
+        c->alloc = *opt->allocator;
+        c->own_alloc = false;
+    } else {
+        c->alloc.alloc = default_alloc;
+        c->alloc.free = default_free;
+        c->alloc.user = nullptr;
+    }
+    c->buf_bytes = lbm_footprint(nx, ny, prec);
+    const size_t cells = (size_t)nx * ny;
+    c->stage_elems = std::min<size_t>(20 * cells, std::max<size_t>(20 * (size_t)nx, (size_t)8 << 20));
+    c->aux_bytes = sizeof(double) * (lbm::kTotalsBlocks * 4 + 4) + 64;
+    c->buf = c->alloc.alloc(c->buf_bytes, c->stream, c->alloc.user);
+    c->stage = c->buf ? (double *)c->alloc.alloc(c->stage_elems * sizeof(double), c->stream, c->alloc.user) : nullptr;
+    c->aux = c->stage ? (double *)c->alloc.alloc(c->aux_bytes, c->stream, c->alloc.user) : nullptr;
+    if (!c->buf || !c->stage || !c->aux) {
+        cudaGetLastError();
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
+    }
+    c->f[0] = c->buf;
+    c->f[1] = (char *)c->buf + c->buf_bytes / 2;
+    c->tot_out = c->aux + lbm::kTotalsBlocks * 4;
+    c->flag = (int *)(c->tot_out + 4);
+    ce = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->aux, 0, c->aux_bytes, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) {
+        lbm_destroy(c);
+        return cuda_fail(nullptr, ce, "device initialisation");
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, double dx, double dt, double gamma, double Pr, const double s[16], int limiter,
+               const lbm_bc *bc, lbm_ctx **out)
+{
+    return lbm_create_ex(nx, ny, dx, dt, gamma, Pr, s, limiter, bc, nullptr, out);
+}
+
+static int rows_per_chunk(const lbm_ctx *c, int planes)
+{
+    const size_t per_row = (size_t)planes * c->P.nx;
+    size_t r = c->stage_elems / per_row;
+    if (r < 1) r = 1;
+    if (r > (size_t)c->P.ny) r = c->P.ny;
+    return (int)r;
+}
+
+int lbm_init(lbm_ctx *c, const double *rho, const double *u, const double *v, const double *T)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!rho || !u || !v || !T) return fail(c, LBM_ERR_ARG, "NULL field");
+    const long long n = (long long)c->P.nx * c->P.ny;
+    for (long long i = 0; i < n; i++)
+        if (!finite_pos(rho[i]) || !finite_pos(T[i]) || !std::isfinite(u[i]) || !std::isfinite(v[i]))
+            return fail(c, LBM_ERR_ARG, "init fields need rho > 0, T > 0 and finite values");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    const int R = rows_per_chunk(c, 4);
+    const int nx = c->P.nx;
+    for (int r0 = 0; r0 < c->P.ny; r0 += R) {
+        const int rows = std::min(R, c->P.ny - r0);
+        const size_t m = (size_t)rows * nx;
+        const double *src[4] = {rho, u, v, T};
+        for (int k = 0; k < 4; k++) {
+            ce = cudaMemcpyAsync(c->stage + k * m, src[k] + (size_t)r0 * nx, m * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "init copy");
+        }
+        ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], c->stage, r0, rows, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "init kernel");
+        ce = cudaStreamSynchronize(c->stream);   // the staging buffer is reused by the next chunk
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "init");
+    }
+    c->initialized = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int n)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (n <= 0) return fail(c, LBM_ERR_STATE, "n must be >= 1");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    for (int s = 0; s < n; s++) {
+        ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
+        ce = lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
+        c->cur ^= 1;
+        c->steps++;
+    }
+    return LBM_OK;
+}
+
+static int moments_impl(lbm_ctx *c, double *rho, double *u, double *v, double *T, double *delta, double *dstar)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "moments before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    const int planes = (rho ? 1 : 0) + (u ? 1 : 0) + (v ? 1 : 0) + (T ? 1 : 0) + (delta ? 16 : 0) + (dstar ? 16 : 0);
+    ce = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "flag reset");
+    const int nx = c->P.nx, ny = c->P.ny;
+    const int R = rows_per_chunk(c, planes > 0 ? planes : 1);
+    for (int r0 = 0; r0 < ny; r0 += R) {
+        const int rows = std::min(R, ny - r0);
+        const size_t m = (size_t)rows * nx;
+        double *p = c->stage;
+        double *d_rho = rho ? p : nullptr; p += rho ? m : 0;
+        double *d_u = u ? p : nullptr; p += u ? m : 0;
+        double *d_v = v ? p : nullptr; p += v ? m : 0;
+        double *d_T = T ? p : nullptr; p += T ? m : 0;
+        double *d_delta = delta ? p : nullptr; p += delta ? 16 * m : 0;
+        double *d_dstar = dstar ? p : nullptr;
+        ce = lbm::launch_moments(c->P, c->prec, c->f[c->cur], r0, rows, d_rho, d_u, d_v, d_T, d_delta, d_dstar,
+                                 c->flag, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "moments kernel");
+        struct { double *h, *d; int planes; } outs[6] = {{rho, d_rho, 1}, {u, d_u, 1}, {v, d_v, 1}, {T, d_T, 1},
+                                                          {delta, d_delta, 16}, {dstar, d_dstar, 16}};
+        for (auto &o : outs) {
+            if (!o.h) continue;
+            for (int k = 0; k < o.planes; k++) {
+                ce = cudaMemcpyAsync(o.h + (size_t)k * nx * ny + (size_t)r0 * nx, o.d + k * m, m * sizeof(double),
+                                     cudaMemcpyDeviceToHost, c->stream);
+                if (ce != cudaSuccess) return cuda_fail(c, ce, "moments copy");
+            }
+        }
+        ce = cudaStreamSynchronize(c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "moments");
+    }
+    int flag = 0;
+    ce = cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "flag copy");
+    if (flag) return fail(c, LBM_ERR_NONFINITE, "a cell has a non-finite value or rho <= 0");
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, double *rho, double *u, double *v, double *T, double *delta)
+{
+    return moments_impl(c, rho, u, v, T, delta, nullptr);
+}
+
+int lbm_moments_central(lbm_ctx *c, double *delta_star)
+{
+    if (c && !delta_star) return fail(c, LBM_ERR_ARG, "delta_star is NULL");
+    return moments_impl(c, nullptr, nullptr, nullptr, nullptr, nullptr, delta_star);
+}
+
+int lbm_totals(lbm_ctx *c, double out[4])
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "totals before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    ce = lbm::launch_totals(c->P, c->prec, c->f[c->cur], c->aux, c->tot_out, c->dx * c->dx, c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "totals kernel");
+    double h[4];
+    ce = cudaMemcpyAsync(h, c->tot_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "totals");
+    for (int k = 0; k < 4; k++) out[k] = h[k];
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx *c, double *f)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!f) return fail(c, LBM_ERR_ARG, "f is NULL");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "get_state before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    const int nx = c->P.nx, ny = c->P.ny;
+    const int R = rows_per_chunk(c, 16);
+    for (int r0 = 0; r0 < ny; r0 += R) {
+        const int rows = std::min(R, ny - r0);
+        const size_t m = (size_t)rows * nx;
+        ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], r0, rows, c->stage, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "pack kernel");
+        for (int q = 0; q < NQ; q++) {
+            ce = cudaMemcpyAsync(f + (size_t)q * nx * ny + (size_t)r0 * nx, c->stage + q * m, m * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "state copy");
+        }
+        ce = cudaStreamSynchronize(c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state");
+    }
+    return LBM_OK;
+}
+
+int lbm_get_state_rows(lbm_ctx *c, int row0, int rows, double *f)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!f) return fail(c, LBM_ERR_ARG, "f is NULL");
+    if (row0 < 0 || rows < 1 || row0 + rows > c->P.ny) return fail(c, LBM_ERR_ARG, "row window outside [0, ny)");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "get_state before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    const int nx = c->P.nx;
+    const int R = rows_per_chunk(c, 16);
+    for (int r = 0; r < rows; r += R) {
+        const int n = std::min(R, rows - r);
+        const size_t m = (size_t)n * nx;
+        ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], row0 + r, n, c->stage, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "pack kernel");
+        for (int q = 0; q < NQ; q++) {
+            ce = cudaMemcpyAsync(f + (size_t)q * nx * rows + (size_t)r * nx, c->stage + q * m, m * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "state copy");
+        }
+        ce = cudaStreamSynchronize(c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state_rows");
+    }
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *c, const double *f)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!f) return fail(c, LBM_ERR_ARG, "f is NULL");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    const int nx = c->P.nx, ny = c->P.ny;
+    const int R = rows_per_chunk(c, 16);
+    for (int r0 = 0; r0 < ny; r0 += R) {
+        const int rows = std::min(R, ny - r0);
+        const size_t m = (size_t)rows * nx;
+        for (int q = 0; q < NQ; q++) {
+            ce = cudaMemcpyAsync(c->stage + q * m, f + (size_t)q * nx * ny + (size_t)r0 * nx, m * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "state copy");
+        }
+        ce = lbm::launch_unpack(c->P, c->prec, c->f[c->cur], r0, rows, c->stage, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "unpack kernel");
+        ce = cudaStreamSynchronize(c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "set_state");
+    }
+    c->initialized = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->alloc.free) {
+        if (c->aux) c->alloc.free(c->aux, c->aux_bytes, c->stream, c->alloc.user);
+        if (c->stage) c->alloc.free(c->stage, c->stage_elems * sizeof(double), c->stream, c->alloc.user);
+        if (c->buf) c->alloc.free(c->buf, c->buf_bytes, c->stream, c->alloc.user);
+    }
+    delete c;
+}
+
+}  // extern "C"

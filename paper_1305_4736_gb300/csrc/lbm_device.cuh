@@ -1,0 +1,267 @@
+// lbm_device.cuh -- device-side arithmetic of the D2V16 MRT FDLBM step.
+//
+// Moment transforms use the rotational symmetry of the velocity set (Sec. II,
+// Fig. 1): each shell of four velocities is a 4-point butterfly
+//   axis shells (1,0),(0,1),(-1,0),(0,-1) x c:
+//     S = sum, X = p0 - p2, Y = p1 - p3, Q = (p0 + p2) - (p1 + p3)
+//   diagonal shells (+,+),(-,+),(-,-),(+,-) x d:
+//     S = sum, X = (p0 - p2) - (p1 - p3), Y = (p0 - p2) + (p1 - p3),
+//     Q = (p0 + p2) - (p1 + p3)
+// after which the 16 rows m_1..m_16 of Appendix A fall into five small blocks:
+//   isotropic  (m1, m4, m5, m14)  <- (S1..S4)
+//   x-odd      (m2, m8, m10, m12) <- (X1..X4)
+//   y-odd      (m3, m9, m11, m13) <- (Y1..Y4)   (m13 row negated)
+//   axis quad  (m6, m16)          <- (Q1, Q2)
+//   diag quad  (m7, m15)          <- (Q3, Q4)
+// The inverse blocks (with dt s_k and the butterfly normalisation folded in)
+// are computed on the host at create time and passed in Params.
+//
+// Equilibria (Appendix A) are evaluated in deviation form about a reference
+// state (rho0, u = 0, T0): every quantity is a difference from the reference,
+// written without cancellation.  The FP64 mode uses the zero reference, for
+// which the formulas are the plain Appendix A closed forms.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr int NQ = 16;
+constexpr int OX = 4;   // column of interior x = 0 (two ghost columns at 2, 3)
+constexpr int OY = 2;   // row of interior y = 0
+
+// Velocity-set constants (Sec. II): shell speeds 1, 6, 2, 3; component of the
+// diagonal shells sqrt2 and 3/sqrt2; eta^2 = 25/4 on shell 1 (Appendix A).
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kD3 = kSqrt2;               // component of shell 3
+constexpr double kD4 = 3.0 / kSqrt2;         // component of shell 4
+constexpr double kW1 = 1.0 + 6.25;           // v^2 + eta^2, shell 1
+constexpr double kEta2 = 6.25;
+
+struct EdgeDev {
+    int kind;
+    double uw, vw, Tw;          // wall velocity / temperature (NEQ wall)
+    double dTw;                 // Tw - T0 (reference-relative, NEQ wall)
+    double feq[NQ];             // fixed equilibrium (minus f^eq0 in deviation mode)
+};
+
+struct Params {
+    int nx, ny, pitch, limiter;
+    long long plane;            // elements per population plane
+    double b, inv_b, dt;
+    // reference state of the deviation form (all zero in FP64 mode)
+    double rho0, T0, P0, e0;
+    double feq0[NQ];            // reference populations f^eq(rho0, 0, 0, T0) (deviation mode)
+    // collision: inverse blocks with dt s_k and the butterfly normalisation
+    double cA[4][2];            // (Delta5, Delta14)         -> S'1..4
+    double cEx[4][3];           // (Delta8, Delta10, Delta12) -> X'1..4
+    double cEy[4][3];           // (Delta9, Delta11, Delta13) -> Y'1..4
+    double cB1[2][2];           // (Delta6, Delta16)          -> Q'1, Q'2
+    double cB2[2][2];           // (Delta7, Delta15)          -> Q'3, Q'4
+    // full inverse blocks with butterfly normalisation (f = M^-1 f_hat)
+    double iA[4][4], iEx[4][4], iEy[4][4], iB1[2][2], iB2[2][2];
+    // energy-flux correction of the collision (Sec. II): Delta8 += q8 P [...], Delta9 += q9 P [...]
+    // q = (s8/s5 - 1) / s8 / (2 dx)
+    double q8, q9;
+    int has_c9;
+    // convection: Courant number c and half-weight h/2 = (1 - c)/4 per shell
+    double cr[4], hh[4];
+    EdgeDev edge[4];            // x-lo, x-hi, y-lo, y-hi
+};
+
+// ---------------------------------------------------------------------------
+// Shell butterflies
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Shells { R S[4], X[4], Y[4], Q[4]; };
+
+template <typename R>
+__host__ __device__ __forceinline__ void butterfly_axis(R p0, R p1, R p2, R p3, R &S, R &X, R &Y, R &Q)
+{
+    const R a = p0 + p2, b = p1 + p3;
+    S = a + b; Q = a - b; X = p0 - p2; Y = p1 - p3;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void butterfly_diag(R p0, R p1, R p2, R p3, R &S, R &X, R &Y, R &Q)
+{
+    const R a = p0 + p2, b = p1 + p3, c = p0 - p2, d = p1 - p3;
+    S = a + b; Q = a - b; X = c - d; Y = c + d;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ Shells<R> shells_of(const R *f)
+{
+    Shells<R> s;
+    butterfly_axis(f[0], f[1], f[2], f[3], s.S[0], s.X[0], s.Y[0], s.Q[0]);
+    butterfly_axis(f[4], f[5], f[6], f[7], s.S[1], s.X[1], s.Y[1], s.Q[1]);
+    butterfly_diag(f[8], f[9], f[10], f[11], s.S[2], s.X[2], s.Y[2], s.Q[2]);
+    butterfly_diag(f[12], f[13], f[14], f[15], s.S[3], s.X[3], s.Y[3], s.Q[3]);
+    return s;
+}
+
+// Inverse butterflies: populations from normalised shell coefficients
+// (axis: S' = S/4, X' = X/2, Y' = Y/2, Q' = Q/4; diagonal: all /4).
+template <typename R>
+__host__ __device__ __forceinline__ void unbutterfly_axis(R S, R X, R Y, R Q, R *p)
+{
+    const R a = S + Q, b = S - Q;
+    p[0] = a + X; p[2] = a - X; p[1] = b + Y; p[3] = b - Y;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void unbutterfly_diag(R S, R X, R Y, R Q, R *p)
+{
+    const R a = S + Q, b = S - Q, c = X + Y, d = X - Y;
+    p[0] = a + c; p[2] = a - c; p[1] = b - d; p[3] = b + d;
+}
+
+// ---------------------------------------------------------------------------
+// Moments from shells (Appendix A rows in block form)
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Moments { R m[NQ]; };   // m[k] = row k+1 of Appendix A applied to f (or g)
+
+template <typename R>
+__host__ __device__ __forceinline__ void conserved_of(const Shells<R> &s, R &rho, R &jx, R &jy, R &e)
+{
+    rho = (s.S[0] + s.S[1]) + (s.S[2] + s.S[3]);
+    jx = s.X[0] + R(6.0) * s.X[1] + R(kD3) * s.X[2] + R(kD4) * s.X[3];
+    jy = s.Y[0] + R(6.0) * s.Y[1] + R(kD3) * s.Y[2] + R(kD4) * s.Y[3];
+    e = R(kW1) * s.S[0] + R(36.0) * s.S[1] + R(4.0) * s.S[2] + R(9.0) * s.S[3];
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ Moments<R> moments_of(const Shells<R> &s)
+{
+    Moments<R> M;
+    conserved_of(s, M.m[0], M.m[1], M.m[2], M.m[3]);
+    M.m[4] = M.m[3] - R(kEta2) * s.S[0];
+    M.m[13] = R(kW1) * s.S[0] + R(1296.0) * s.S[1] + R(16.0) * s.S[2] + R(81.0) * s.S[3];
+    const R x8 = R(kW1) * s.X[0] + R(216.0) * s.X[1] + R(4.0 * kSqrt2) * s.X[2] + R(27.0 / kSqrt2) * s.X[3];
+    const R y8 = R(kW1) * s.Y[0] + R(216.0) * s.Y[1] + R(4.0 * kSqrt2) * s.Y[2] + R(27.0 / kSqrt2) * s.Y[3];
+    M.m[7] = x8;
+    M.m[8] = y8;
+    M.m[9] = x8 - R(kEta2) * s.X[0];
+    M.m[10] = y8 - R(kEta2) * s.Y[0];
+    M.m[11] = s.X[0] + R(216.0) * s.X[1];
+    M.m[12] = -(s.Y[0] + R(216.0) * s.Y[1]);
+    M.m[5] = s.Q[0] + R(36.0) * s.Q[1];
+    M.m[15] = R(kW1) * s.Q[0] + R(1296.0) * s.Q[1];
+    M.m[6] = R(2.0) * s.Q[2] + R(4.5) * s.Q[3];
+    M.m[14] = R(8.0) * s.Q[2] + R(40.5) * s.Q[3];
+    return M;
+}
+
+// ---------------------------------------------------------------------------
+// Equilibria (Appendix A) in deviation form.
+// Inputs: drho = rho - rho0, j, dP = P - P0 (u0 = 0).  Output: f_hat^eq - f_hat^eq0,
+// all 16 rows.  With rho0 = P0 = T0 = e0 = 0 this is f_hat^eq itself.
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__host__ __device__ __forceinline__ void feq_hat_dev(const Params &P, R drho, R jx, R jy, R dP, R ir, R *q)
+{
+    const R b = R(P.b);
+    const R ux = jx * ir, uy = jy * ir;
+    const R jx2 = jx * ux, jy2 = jy * uy, J2 = jx2 + jy2;
+    const R Pt = Dev ? R(P.P0) + dP : dP;                 // total pressure
+    const R et = Dev ? R(P.e0) + b * dP + J2 : b * dP + J2; // total e
+    const R dxy = jx2 - jy2;
+    q[0] = drho;
+    q[1] = jx;
+    q[2] = jy;
+    q[3] = b * dP + J2;
+    q[4] = R(2.0) * dP + J2;
+    q[5] = dxy;
+    q[6] = jx * uy;
+    const R e2p = et + R(2.0) * Pt;
+    q[7] = e2p * ux;
+    q[8] = e2p * uy;
+    const R g4 = R(4.0) * Pt + J2;
+    q[9] = g4 * ux;
+    q[10] = g4 * uy;
+    q[11] = (R(2.0) * Pt + dxy) * ux;
+    q[12] = (dxy - R(2.0) * Pt) * uy;
+    const R T = Pt * ir;
+    R iso;
+    if (Dev) iso = ir * (dP * (Pt + R(P.P0)) - R(P.P0 * P.T0) * drho);   // P^2/rho - P0^2/rho0
+    else     iso = Pt * T;                                               // P^2 / rho
+    q[13] = R(2.0) * (b + R(2.0)) * iso + (R(6.0) + b) * T * J2 + J2 * J2 * ir;
+    const R k = (b + R(4.0)) * Pt + J2;
+    q[14] = k * ux * uy;
+    q[15] = k * dxy * ir;
+}
+
+// Populations from a full moment vector q (16 rows) with the full inverse blocks.
+template <typename R>
+__host__ __device__ __forceinline__ void pop_from_moments(const Params &P, const R *q, R *f)
+{
+    R S[4], X[4], Y[4], Q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        S[k] = R(P.iA[k][0]) * q[0] + R(P.iA[k][1]) * q[3] + R(P.iA[k][2]) * q[4] + R(P.iA[k][3]) * q[13];
+        X[k] = R(P.iEx[k][0]) * q[1] + R(P.iEx[k][1]) * q[7] + R(P.iEx[k][2]) * q[9] + R(P.iEx[k][3]) * q[11];
+        Y[k] = R(P.iEy[k][0]) * q[2] + R(P.iEy[k][1]) * q[8] + R(P.iEy[k][2]) * q[10] + R(P.iEy[k][3]) * q[12];
+    }
+    Q[0] = R(P.iB1[0][0]) * q[5] + R(P.iB1[0][1]) * q[15];
+    Q[1] = R(P.iB1[1][0]) * q[5] + R(P.iB1[1][1]) * q[15];
+    Q[2] = R(P.iB2[0][0]) * q[6] + R(P.iB2[0][1]) * q[14];
+    Q[3] = R(P.iB2[1][0]) * q[6] + R(P.iB2[1][1]) * q[14];
+    unbutterfly_axis(S[0], X[0], Y[0], Q[0], f + 0);
+    unbutterfly_axis(S[1], X[1], Y[1], Q[1], f + 4);
+    unbutterfly_diag(S[2], X[2], Y[2], Q[2], f + 8);
+    unbutterfly_diag(S[3], X[3], Y[3], Q[3], f + 12);
+}
+
+// ---------------------------------------------------------------------------
+// Flux limiter (Sec. III).  For one population along one axis, in upwind
+// order (f_{J-2s}, f_{J-s}, f_J, f_{J+s}), return
+//   (F_out - F_in) = (f_J - f_{J-s}) + h [psi_J D+_J - psi_{J-s} D+_{J-s}]
+// with D+_J = f_{J+s} - f_J.  psi(theta) D+ is evaluated without the
+// division: for the MC limiter it equals minmod(2 D-, (D- + D+)/2, 2 D+)
+// (0 when D- D+ <= 0), for Lax-Wendroff D+, for upwind 0.  The magnitude
+// comparisons and the sign logic run on the integer pipe; they are exact.
+// `hh` is h/2 = (1 - c)/4 because mc2 returns twice the slope.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double mc2(double a, double b)
+{
+    // 2 * minmod(2a, (a+b)/2, 2b) = sign * min(4|a|, 4|b|, |a+b|)
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long mask = 0x7fffffffffffffffLL;
+    const long long aa = ia & mask, ab = ib & mask;
+    const long long m = aa < ab ? aa : ab;
+    const double m4 = 4.0 * __longlong_as_double(m);
+    const long long id = __double_as_longlong(a + b) & mask;
+    const long long im4 = __double_as_longlong(m4);
+    const long long r = im4 < id ? im4 : id;
+    const bool same = ((ia ^ ib) >= 0) && (m != 0);
+    return __longlong_as_double(same ? (r | (ib & ~mask)) : 0LL);
+}
+
+__device__ __forceinline__ float mc2(float a, float b)
+{
+    const int ia = __float_as_int(a), ib = __float_as_int(b);
+    const int mask = 0x7fffffff;
+    const int aa = ia & mask, ab = ib & mask;
+    const int m = aa < ab ? aa : ab;
+    const float m4 = 4.0f * __int_as_float(m);
+    const int id = __float_as_int(a + b) & mask;
+    const int im4 = __float_as_int(m4);
+    const int r = im4 < id ? im4 : id;
+    const bool same = ((ia ^ ib) >= 0) && (m != 0);
+    return __int_as_float(same ? (r | (ib & ~mask)) : 0);
+}
+
+template <typename R, int Lim>
+__device__ __forceinline__ R flux_diff(R fmm, R fm, R f0, R fp, R hh)
+{
+    const R d1 = f0 - fm;
+    if (Lim == 2) return d1;                     // upwind
+    const R d2 = fp - f0;
+    if (Lim == 1) return d1 + R(2.0) * hh * (d2 - d1);   // Lax-Wendroff: psi = 1
+    const R d0 = fm - fmm;
+    return d1 + hh * (mc2(d1, d2) - mc2(d0, d1));
+}
+
+}  // namespace lbm

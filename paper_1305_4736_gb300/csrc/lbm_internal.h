@@ -1,0 +1,33 @@
+// lbm_internal.h -- launchers shared between the host API and the kernel units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Tile of the fused step kernel: TX x TY cells, one thread per cell.
+constexpr int kTX = 32;
+constexpr int kTY = 8;
+// Fixed grid of the first totals pass (the result is deterministic for a given size).
+constexpr int kTotalsBlocks = 512;
+constexpr int kTotalsThreads = 256;
+
+// All launchers enqueue on `st` and return the launch status.
+// `prec` is the storage precision (0 = float64 f, 1 = float32 deviation g).
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows,
+                        cudaStream_t st);
+cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
+cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st);
+cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, int rows,
+                           double *rho, double *u, double *v, double *T, double *delta,
+                           double *dstar, int *flag, cudaStream_t st);
+cudaError_t launch_totals(const Params &P, int prec, const void *f, double *partial, double *out,
+                          double scale, cudaStream_t st);
+cudaError_t launch_pack(const Params &P, int prec, const void *f, int row0, int rows, double *out,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const Params &P, int prec, void *f, int row0, int rows, const double *in,
+                          cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,560 @@
+// lbm_kernels.cu -- CUDA kernels of the D2V16 MRT flux-limiter FDLBM step (sm_103a).
+//
+//   k_ghost    ghost cells of every edge (Sec. IV.A, IV.C, V)
+//   k_step     fused step: local rho/u on the tile + 1 ring, central-difference
+//              grad u, MRT collision with the energy-flux correction (Eq. 3,
+//              Sec. II), flux-limited x and y convection and the forward-Euler
+//              update of Sec. III, one write per population
+//   k_init     f = M^-1 f_hat^eq(rho, u, v, T) per cell (Appendix A)
+//   k_moments  rho, u, v, T, Delta = M f - f_hat^eq, Delta* = M*(f - f^eq) (Sec. V)
+//   k_totals_* deterministic two-pass float64 totals of rho, j, e
+//   k_pack / k_unpack  interior populations to / from a dense float64 buffer
+//
+// Storage: population planes q = 0..15 of (ny + 4) rows by `pitch` columns;
+// interior cell (x, y) at row y + 2, column x + 4.  R = double stores f;
+// R = float stores g = f - f^eq0 (deviation mode).
+#include "lbm_internal.h"
+
+namespace lbm {
+
+__device__ __forceinline__ constexpr int sgn_x(int q)
+{
+    return q < 8 ? ((q & 3) == 0 ? 1 : ((q & 3) == 2 ? -1 : 0)) : (((q & 3) == 0 || (q & 3) == 3) ? 1 : -1);
+}
+__device__ __forceinline__ constexpr int sgn_y(int q)
+{
+    return q < 8 ? ((q & 3) == 1 ? 1 : ((q & 3) == 3 ? -1 : 0)) : (((q & 3) <= 1) ? 1 : -1);
+}
+
+// Cells whose flow velocity the central differences of an interior cell read:
+// the interior plus the first ghost layer of the cross (never a corner).
+__device__ __forceinline__ bool u_cell(int x, int y, int nx, int ny)
+{
+    return (x >= -1 && x <= nx && y >= 0 && y < ny) || (y >= -1 && y <= ny && x >= 0 && x < nx);
+}
+
+template <typename R>
+__device__ __forceinline__ void load16(const R *__restrict__ f, long long plane, long long c, R *out)
+{
+#pragma unroll
+    for (int q = 0; q < NQ; q++) out[q] = f[q * plane + c];
+}
+
+// ---------------------------------------------------------------------------
+// Collision (Eq. 3 with the energy-flux correction of Sec. II):
+//   out = dt M^-1 S (f_hat - f_hat^eq), residuals of rows 1..4 are zero.
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R drho, R jx, R jy, R de,
+                                        R ir, R dxux, R dyux, R dxuy, R dyuy, R *out)
+{
+    const Moments<R> M = moments_of(sh);
+    const R ux = jx * ir, uy = jy * ir;
+    const R J2 = jx * ux + jy * uy;
+    const R dP = (de - J2) * R(P.inv_b);
+    R q[NQ];
+    feq_hat_dev<R, Dev>(P, drho, jx, jy, dP, ir, q);
+    R D[NQ];
+#pragma unroll
+    for (int k = 4; k < NQ; k++) D[k] = M.m[k] - q[k];
+    if (P.has_c9) {
+        const R Pt = Dev ? R(P.P0) + dP : dP;
+        const R div = dxux + dyuy, shr = dxuy + dyux;
+        const R fb = R(4.0) * R(P.inv_b);
+        D[7] += R(P.q8) * Pt * (ux * (R(4.0) * dxux - fb * div) + R(2.0) * uy * shr);
+        D[8] += R(P.q9) * Pt * (R(2.0) * ux * shr + uy * (R(4.0) * dyuy - fb * div));
+    }
+    R S[4], X[4], Y[4], Q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        S[k] = R(P.cA[k][0]) * D[4] + R(P.cA[k][1]) * D[13];
+        X[k] = R(P.cEx[k][0]) * D[7] + R(P.cEx[k][1]) * D[9] + R(P.cEx[k][2]) * D[11];
+        Y[k] = R(P.cEy[k][0]) * D[8] + R(P.cEy[k][1]) * D[10] + R(P.cEy[k][2]) * D[12];
+    }
+    Q[0] = R(P.cB1[0][0]) * D[5] + R(P.cB1[0][1]) * D[15];
+    Q[1] = R(P.cB1[1][0]) * D[5] + R(P.cB1[1][1]) * D[15];
+    Q[2] = R(P.cB2[0][0]) * D[6] + R(P.cB2[0][1]) * D[14];
+    Q[3] = R(P.cB2[1][0]) * D[6] + R(P.cB2[1][1]) * D[14];
+    unbutterfly_axis(S[0], X[0], Y[0], Q[0], out + 0);
+    unbutterfly_axis(S[1], X[1], Y[1], Q[1], out + 4);
+    unbutterfly_diag(S[2], X[2], Y[2], Q[2], out + 8);
+    unbutterfly_diag(S[3], X[3], Y[3], Q[3], out + 12);
+}
+
+template <typename R, bool Dev>
+__device__ __forceinline__ void velocity_of(const Params &P, const R *f, R &ux, R &uy)
+{
+    const Shells<R> s = shells_of(f);
+    R drho, jx, jy, de;
+    conserved_of(s, drho, jx, jy, de);
+    const R rho = Dev ? R(P.rho0) + drho : drho;
+    const R ir = R(1.0) / rho;
+    ux = jx * ir;
+    uy = jy * ir;
+}
+
+// ---------------------------------------------------------------------------
+// Fused step
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev, int Lim>
+__global__ void __launch_bounds__(kTX * kTY)
+k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restrict__ fout)
+{
+    __shared__ R su[kTY + 2][kTX + 2];
+    __shared__ R sv[kTY + 2][kTX + 2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int ix = x0 + tx, iy = y0 + ty;
+    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    const long long plane = P.plane;
+    const bool inside = (ix < nx) && (iy < ny);
+    const long long c0 = (long long)(iy + OY) * pitch + (ix + OX);
+
+    R f[NQ];
+    Shells<R> sh;
+    R drho = R(0), jx = R(0), jy = R(0), de = R(0), ir = R(1);
+    if (inside) {
+        load16(fin, plane, c0, f);
+        sh = shells_of(f);
+        conserved_of(sh, drho, jx, jy, de);
+        const R rho = Dev ? R(P.rho0) + drho : drho;
+        ir = R(1.0) / rho;
+        su[ty + 1][tx + 1] = jx * ir;
+        sv[ty + 1][tx + 1] = jy * ir;
+    } else if (u_cell(ix, iy, nx, ny)) {
+        R g[NQ];
+        load16(fin, plane, c0, g);
+        R a, b;
+        velocity_of<R, Dev>(P, g, a, b);
+        su[ty + 1][tx + 1] = a;
+        sv[ty + 1][tx + 1] = b;
+    }
+    // ring of the tile: bottom row, top row, left column, right column
+    const int t = ty * kTX + tx;
+    if (t < 2 * (kTX + kTY)) {
+        int rx, ry, lx, ly;
+        if (t < kTX) { rx = x0 + t; ry = y0 - 1; lx = t + 1; ly = 0; }
+        else if (t < 2 * kTX) { rx = x0 + t - kTX; ry = y0 + kTY; lx = t - kTX + 1; ly = kTY + 1; }
+        else if (t < 2 * kTX + kTY) { rx = x0 - 1; ry = y0 + t - 2 * kTX; lx = 0; ly = t - 2 * kTX + 1; }
+        else { rx = x0 + kTX; ry = y0 + t - 2 * kTX - kTY; lx = kTX + 1; ly = t - 2 * kTX - kTY + 1; }
+        if (u_cell(rx, ry, nx, ny)) {
+            R g[NQ];
+            load16(fin, plane, (long long)(ry + OY) * pitch + (rx + OX), g);
+            R a, b;
+            velocity_of<R, Dev>(P, g, a, b);
+            su[ly][lx] = a;
+            sv[ly][lx] = b;
+        }
+    }
+    __syncthreads();
+    if (!inside) return;
+
+    // central differences (the 1/(2 dx) factor is folded into q8, q9)
+    const int lx = tx + 1, ly = ty + 1;
+    const R dxux = su[ly][lx + 1] - su[ly][lx - 1];
+    const R dyux = su[ly + 1][lx] - su[ly - 1][lx];
+    const R dxuy = sv[ly][lx + 1] - sv[ly][lx - 1];
+    const R dyuy = sv[ly + 1][lx] - sv[ly - 1][lx];
+
+    R acc[NQ];
+    collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] = f[q] - acc[q];
+
+    // limited convection: x and y projections, both from f^n (Sec. III)
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const int sx = sgn_x(q), sy = sgn_y(q);
+        const int shell = q >> 2;
+        const R hh = R(P.hh[shell]);
+        const R *fq = fin + q * plane;
+        R tot = R(0);
+        if (sx != 0) {
+            const R fmm = fq[c0 - 2 * sx], fm = fq[c0 - sx], fp = fq[c0 + sx];
+            tot += flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+        }
+        if (sy != 0) {
+            const long long sp = (long long)sy * pitch;
+            const R fmm = fq[c0 - 2 * sp], fm = fq[c0 - sp], fp = fq[c0 + sp];
+            tot += flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+        }
+        fout[q * plane + c0] = acc[q] - R(P.cr[shell]) * tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ghost cells.  One thread per ghost cell: x edges cover the interior rows,
+// y edges the interior columns (the stencil is a cross; corners are unused).
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
+{
+    const int nx = P.nx, ny = P.ny;
+    const long long plane = P.plane;
+    const int n_x = 4 * ny, n_all = 4 * ny + 4 * nx;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_all) return;
+    int edge, gx, gy, sx, sy, mx, my, n, k, along;
+    if (idx < n_x) {
+        edge = idx / (2 * ny);            // 0 = x-lo, 1 = x-hi
+        const int r = idx % (2 * ny);
+        k = r / ny + 1;                   // ghost layer 1 or 2
+        along = r % ny;
+        n = nx;
+        gy = sy = my = along;
+        if (edge == 0) { gx = -k; mx = k - 1; } else { gx = nx - 1 + k; mx = nx - k; }
+        const int kind = P.edge[edge].kind;
+        sx = (kind == 0) ? ((gx % n) + n) % n : (edge == 0 ? 0 : nx - 1);
+    } else {
+        const int j = idx - n_x;
+        edge = 2 + j / (2 * nx);          // 2 = y-lo, 3 = y-hi
+        const int r = j % (2 * nx);
+        k = r / nx + 1;
+        along = r % nx;
+        n = ny;
+        gx = sx = mx = along;
+        if (edge == 2) { gy = -k; my = k - 1; } else { gy = ny - 1 + k; my = ny - k; }
+        const int kind = P.edge[edge].kind;
+        sy = (kind == 0) ? ((gy % n) + n) % n : (edge == 2 ? 0 : ny - 1);
+    }
+    mx = mx < 0 ? 0 : (mx >= nx ? nx - 1 : mx);
+    my = my < 0 ? 0 : (my >= ny ? ny - 1 : my);
+    const EdgeDev &E = P.edge[edge];
+    const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
+    if (E.kind == 0 || E.kind == 1) {                       // periodic / zero gradient
+        const long long cs = (long long)(sy + OY) * P.pitch + (sx + OX);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) f[q * plane + cg] = f[q * plane + cs];
+    } else if (E.kind == 2) {                               // fixed equilibrium
+#pragma unroll
+        for (int q = 0; q < NQ; q++) f[q * plane + cg] = R(E.feq[q]);
+    } else {                                                // non-equilibrium extrapolation wall
+        const long long cm = (long long)(my + OY) * P.pitch + (mx + OX);
+        R g[NQ];
+        load16(f, plane, cm, g);
+        const Shells<R> s = shells_of(g);
+        R drho, jx, jy, de;
+        conserved_of(s, drho, jx, jy, de);
+        const R rho = Dev ? R(P.rho0) + drho : drho;
+        const R ir = R(1.0) / rho;
+        const R J2 = (jx * jx + jy * jy) * ir;
+        const R dP = (de - J2) * R(P.inv_b);
+        // ghost state: rho_g = rho_m, j_g = 2 rho_m u_w - j_m, P_g = rho_m (2 T_w - T_m)
+        const R jgx = R(2.0) * rho * R(E.uw) - jx;
+        const R jgy = R(2.0) * rho * R(E.vw) - jy;
+        const R dPg = Dev ? R(2.0 * P.rho0 * E.dTw) + R(2.0) * drho * R(E.Tw) - dP
+                          : R(2.0) * rho * R(E.Tw) - dP;
+        R qm[NQ], qg[NQ], d[NQ], fd[NQ];
+        feq_hat_dev<R, Dev>(P, drho, jx, jy, dP, ir, qm);
+        feq_hat_dev<R, Dev>(P, drho, jgx, jgy, dPg, ir, qg);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) d[q] = qg[q] - qm[q];
+        pop_from_moments(P, d, fd);
+#pragma unroll
+        for (int q = 0; q < NQ; q++) f[q * plane + cg] = g[q] + fd[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation from macroscopic fields (float64 arithmetic in both modes).
+// fields = [4][rows][nx] (rho, u, v, T) for interior rows row0 .. row0+rows-1.
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, const double *__restrict__ fields,
+                       int row0, int rows)
+{
+    const int nx = P.nx;
+    const long long n = (long long)rows * nx;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % nx), y = row0 + (int)(i / nx);
+    const double rho = fields[i], ux = fields[n + i], uy = fields[2 * n + i], T = fields[3 * n + i];
+    const double drho = rho - P.rho0;
+    const double dP = rho * T - P.P0;
+    double q[NQ], g[NQ];
+    feq_hat_dev<double, Dev>(P, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
+    pop_from_moments(P, q, g);
+    const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+#pragma unroll
+    for (int qq = 0; qq < NQ; qq++) f[qq * P.plane + c] = R(g[qq]);
+}
+
+// ---------------------------------------------------------------------------
+// Moments (float64): rho, u, v, T, Delta and Delta* of interior rows.
+// ---------------------------------------------------------------------------
+template <bool Dev>
+__device__ __forceinline__ void moment_rows(const Params &P, const double *g, double &rho, double &ux,
+                                            double &uy, double &T, double *D, double &ir)
+{
+    const Shells<double> s = shells_of(g);
+    const Moments<double> M = moments_of(s);
+    const double drho = M.m[0], jx = M.m[1], jy = M.m[2], de = M.m[3];
+    rho = Dev ? P.rho0 + drho : drho;
+    ir = 1.0 / rho;
+    ux = jx * ir;
+    uy = jy * ir;
+    const double J2 = jx * ux + jy * uy;
+    const double dP = (de - J2) * P.inv_b;
+    T = (Dev ? P.P0 + dP : dP) * ir;
+    double q[NQ];
+    feq_hat_dev<double, Dev>(P, drho, jx, jy, dP, ir, q);
+#pragma unroll
+    for (int k = 0; k < NQ; k++) D[k] = M.m[k] - q[k];
+}
+
+// velocity of population i (Sec. II)
+__device__ __forceinline__ void velocity_i(int i, double &vx, double &vy)
+{
+    const double sp[4] = {1.0, 6.0, kD3, kD4};
+    vx = sgn_x(i) * sp[i >> 2];
+    vy = sgn_y(i) * sp[i >> 2];
+}
+
+template <typename R, bool Dev>
+__global__ void k_moments(const __grid_constant__ Params P, const R *__restrict__ f, int row0, int rows,
+                          double *rho_o, double *u_o, double *v_o, double *T_o, double *delta_o,
+                          double *dstar_o, int *flag)
+{
+    const int nx = P.nx;
+    const long long n = (long long)rows * nx;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % nx), y = row0 + (int)(i / nx);
+    const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+    double g[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) g[q] = (double)f[q * P.plane + c];
+    double rho, ux, uy, T, D[NQ], ir;
+    moment_rows<Dev>(P, g, rho, ux, uy, T, D, ir);
+    if (!(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(T)) atomicOr(flag, 1);
+    if (rho_o) rho_o[i] = rho;
+    if (u_o) u_o[i] = ux;
+    if (v_o) v_o[i] = uy;
+    if (T_o) T_o[i] = T;
+    if (delta_o) {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) delta_o[k * n + i] = D[k];
+    }
+    if (dstar_o) {
+        // f - f^eq = M^-1 Delta, then the rows of M* at w = v_i - u (Appendix A)
+        double fn[NQ], out[NQ];
+        pop_from_moments(P, D, fn);
+#pragma unroll
+        for (int k = 0; k < NQ; k++) out[k] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            double vx, vy;
+            velocity_i(q, vx, vy);
+            const double wx = vx - ux, wy = vy - uy;
+            const double w2 = wx * wx + wy * wy;
+            const double we = w2 + (q < 4 ? kEta2 : 0.0);
+            const double dd = wx * wx - wy * wy;
+            const double a = fn[q];
+            out[0] += a;
+            out[1] += a * wx;
+            out[2] += a * wy;
+            out[3] += a * we;
+            out[4] += a * w2;
+            out[5] += a * dd;
+            out[6] += a * wx * wy;
+            out[7] += a * wx * we;
+            out[8] += a * wy * we;
+            out[9] += a * wx * w2;
+            out[10] += a * wy * w2;
+            out[11] += a * wx * dd;
+            out[12] += a * wy * dd;
+            out[13] += a * w2 * we;
+            out[14] += a * wx * wy * we;
+            out[15] += a * dd * we;
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; k++) dstar_o[k * n + i] = out[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Totals: pass 1 (fixed grid, grid-stride, block tree) and pass 2 (one block).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R, bool Dev>
+__global__ void __launch_bounds__(kTotalsThreads)
+k_totals_partial(const __grid_constant__ Params P, const R *__restrict__ f, double *partial)
+{
+    __shared__ double red[kTotalsThreads / 32][4];
+    const long long n = (long long)P.nx * P.ny;
+    double a[4] = {0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % P.nx), y = (int)(i / P.nx);
+        const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+        double g[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) g[q] = (double)f[q * P.plane + c];
+        const Shells<double> s = shells_of(g);
+        double drho, jx, jy, de;
+        conserved_of(s, drho, jx, jy, de);
+        a[0] += Dev ? P.rho0 + drho : drho;
+        a[1] += jx;
+        a[2] += jy;
+        a[3] += Dev ? P.e0 + de : de;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double v = warp_sum(a[k]);
+        if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int j = 0; j < kTotalsThreads / 32; j++) v += red[j][threadIdx.x];
+        partial[blockIdx.x * 4 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_totals_final(const double *__restrict__ partial, int nblocks, double scale, double *out)
+{
+    __shared__ double red[32][4];
+    double a[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 4; k++) a[k] += partial[b * 4 + k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double v = warp_sum(a[k]);
+        if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); j++) v += red[j][threadIdx.x];
+        out[threadIdx.x] = v * scale;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pack / unpack interior populations (float64 f; deviation mode adds f^eq0).
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__global__ void k_pack(const __grid_constant__ Params P, const R *__restrict__ f, int row0, int rows,
+                       double *out)
+{
+    const long long n = (long long)rows * P.nx;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % P.nx), y = row0 + (int)(i / P.nx);
+    const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) out[q * n + i] = (double)f[q * P.plane + c] + (Dev ? P.feq0[q] : 0.0);
+}
+
+template <typename R, bool Dev>
+__global__ void k_unpack(const __grid_constant__ Params P, R *__restrict__ f, int row0, int rows,
+                         const double *__restrict__ in)
+{
+    const long long n = (long long)rows * P.nx;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % P.nx), y = row0 + (int)(i / P.nx);
+    const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) f[q * P.plane + c] = R(in[q * n + i] - (Dev ? P.feq0[q] : 0.0));
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows,
+                        cudaStream_t st)
+{
+    const long long n = (long long)rows * P.nx;
+    if (n == 0) return cudaSuccess;
+    if (prec == 0) k_init<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, fields, row0, rows);
+    else k_init<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, fields, row0, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st)
+{
+    const int n = 4 * (P.nx + P.ny);
+    if (prec == 0) k_ghost<double, false><<<blocks_for(n, 128), 128, 0, st>>>(P, (double *)f);
+    else k_ghost<float, true><<<blocks_for(n, 128), 128, 0, st>>>(P, (float *)f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st)
+{
+    const dim3 block(kTX, kTY);
+    const dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
+    if (prec == 0) {
+        const double *a = (const double *)fin;
+        double *b = (double *)fout;
+        if (P.limiter == 0) k_step<double, false, 0><<<grid, block, 0, st>>>(P, a, b);
+        else if (P.limiter == 1) k_step<double, false, 1><<<grid, block, 0, st>>>(P, a, b);
+        else k_step<double, false, 2><<<grid, block, 0, st>>>(P, a, b);
+    } else {
+        const float *a = (const float *)fin;
+        float *b = (float *)fout;
+        if (P.limiter == 0) k_step<float, true, 0><<<grid, block, 0, st>>>(P, a, b);
+        else if (P.limiter == 1) k_step<float, true, 1><<<grid, block, 0, st>>>(P, a, b);
+        else k_step<float, true, 2><<<grid, block, 0, st>>>(P, a, b);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, int rows, double *rho,
+                           double *u, double *v, double *T, double *delta, double *dstar, int *flag,
+                           cudaStream_t st)
+{
+    const long long n = (long long)rows * P.nx;
+    if (n == 0) return cudaSuccess;
+    if (prec == 0)
+        k_moments<double, false><<<blocks_for(n, 128), 128, 0, st>>>(P, (const double *)f, row0, rows, rho, u, v,
+                                                                    T, delta, dstar, flag);
+    else
+        k_moments<float, true><<<blocks_for(n, 128), 128, 0, st>>>(P, (const float *)f, row0, rows, rho, u, v, T,
+                                                                  delta, dstar, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const Params &P, int prec, const void *f, double *partial, double *out, double scale,
+                          cudaStream_t st)
+{
+    if (prec == 0)
+        k_totals_partial<double, false><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const double *)f, partial);
+    else
+        k_totals_partial<float, true><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const float *)f, partial);
+    k_totals_final<<<1, 256, 0, st>>>(partial, kTotalsBlocks, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Params &P, int prec, const void *f, int row0, int rows, double *out,
+                        cudaStream_t st)
+{
+    const long long n = (long long)rows * P.nx;
+    if (n == 0) return cudaSuccess;
+    if (prec == 0) k_pack<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (const double *)f, row0, rows, out);
+    else k_pack<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (const float *)f, row0, rows, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Params &P, int prec, void *f, int row0, int rows, const double *in,
+                          cudaStream_t st)
+{
+    const long long n = (long long)rows * P.nx;
+    if (n == 0) return cudaSuccess;
+    if (prec == 0) k_unpack<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, row0, rows, in);
+    else k_unpack<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, row0, rows, in);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

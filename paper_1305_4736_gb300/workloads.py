@@ -135,12 +135,12 @@ def shock_interface(nx: int = 4096, ny: int = 1024, seed: int = SEED, steps: int
                     p0: float = 1.0) -> Problem:
     """Mach-1.5 shock in heavy gas (rho = 4, p = p0) hitting a light gas (rho = 1, p = p0)
     across a sinusoidal interface x_i(y) = 0.6 Lx/4 + 0.02 Ly cos(2 pi y/Ly + phi), phi seeded.
-    Lx = 4 Ly, Ly = 1, dx = Ly/ny, dt = 5e-5 (1024/ny); gamma = 1.4, all s = 1e4;
+    Lx = 4 Ly, Ly = 1, dx = Ly/ny, dt = 5e-5 (s dt = 0.5 at every size); gamma = 1.4, all s = 1e4;
     x-lo fixed equilibrium (post-shock), x-hi zero-gradient, periodic y."""
     gamma = 1.4
     Lx, Ly = 4.0 * (nx / (4 * ny)), 1.0
     dx = Ly / ny
-    dt = 5e-5 * (1024.0 / ny)
+    dt = 5e-5
     phi = np.random.default_rng(seed).uniform(0.0, 2.0 * math.pi)
     rho_s, u_s, p_s, speed = normal_shock_state(4.0, p0, 1.5, gamma)
     x = _centres(nx, dx)[None, :]
@@ -164,11 +164,12 @@ def shear_layer(n: int = 8192, seed: int = SEED, steps: int = 2000, ny: int | No
     u_x = 0.05 tanh((y - 1/4)/delta) for y < 1/2 and 0.05 tanh((3/4 - y)/delta) above,
     delta = 1/160; v = seeded 8-mode sine perturbation rescaled to max |v| = 1e-3.
     gamma = 1.4, Pr = 0.71: s_5..7 = 5e4, s_8..9 = 3.55e4, others 1e5; dx = 1/n,
-    dt = 1e-5 (8192/n).  `ny` (default n) allows rectangular test grids with the same dx."""
+    dt = 1e-5 at every size (s dt <= 1).  `ny` (default n) allows rectangular test grids
+    with the same dx."""
     nx = n
     ny = n if ny is None else ny
     dx = 1.0 / n
-    dt = 1e-5 * (8192.0 / n)
+    dt = 1e-5
     rng = np.random.default_rng(seed)
     a = rng.uniform(-1.0, 1.0, 8)
     ph = rng.uniform(0.0, 2.0 * math.pi, 8)

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C interface against the CPU oracle.
+
+Bar (FP64 mode): max relative error <= 1e-10 on rho, u, T (field-normwise:
+max|gpu - oracle| / max|oracle|, u as a vector) after the stated steps; the
+two sides differ only in summation order and in the division-free limiter
+form (Sec. III, reading A6), both Lipschitz, so differences stay at round-off.
+Sizes are chosen so the oracle finishes in seconds while the grids span several
+32 x 8 tiles with ragged tails.  FP32 deviation mode: L1 relative <= 1e-4 and
+max relative <= 1e-3 on rho, u, T; conserved totals drift <= 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _gpu_helpers import fp64_errors, l1_rel, max_rel, run_both, vel_max_rel
+from paper_1305_4736_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1305_4736_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def _assert_fp64(errs, tol=TOL):
+    for k, v in errs.items():
+        assert v <= tol, f"{k}: {v:.3e} > {tol:.0e} ({errs})"
+
+
+def test_sod_1000_steps(orc, lbm):
+    p = wl.sod(200, 4)
+    s, O = run_both(orc, lbm, p, 1000)
+    _assert_fp64(fp64_errors(s, O))
+
+
+@pytest.mark.parametrize("Pr", [0.5, 1.0, 2.0])
+def test_couette_1000_steps(orc, lbm, Pr):
+    p = wl.couette(Pr, nx=4, ny=200)
+    s, O = run_both(orc, lbm, p, 1000)
+    _assert_fp64(fp64_errors(s, O))
+
+
+def test_shock_interface_reduced(orc, lbm):
+    p = wl.shock_interface(nx=150, ny=38, steps=300)      # ragged in both directions
+    s, O = run_both(orc, lbm, p, 300)
+    _assert_fp64(fp64_errors(s, O))
+
+
+def test_shear_layer_reduced(orc, lbm):
+    p = wl.shear_layer(100, ny=70)                         # same dx, dt as the 100^2 layer
+    s, O = run_both(orc, lbm, p, 300)
+    _assert_fp64(fp64_errors(s, O))
+
+
+@pytest.mark.parametrize("limiter", [1, 2])
+def test_lax_wendroff_and_upwind_variants(orc, lbm, limiter):
+    p = wl.shock_interface(nx=70, ny=20, steps=100)
+    s, O = run_both(orc, lbm, p, 100, limiter=limiter)
+    _assert_fp64(fp64_errors(s, O))
+
+
+def test_every_boundary_kind(orc, lbm):
+    """NEQ walls on x (moving, heated), fixed equilibrium on y, Pr != 1, ragged grid."""
+    p = wl.shear_layer(64, ny=45)
+    p.nx, p.ny = 37, 45
+    p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:45, :37]) for a in (p.rho, p.ux, p.uy, p.T))
+    p.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_EQUILIBRIUM, 0.98, -0.01, 0.0, 1.02)]
+    s, O = run_both(orc, lbm, p, 200)
+    _assert_fp64(fp64_errors(s, O))
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (2, 3), (33, 9), (31, 7)])
+def test_degenerate_and_tile_edge_sizes(orc, lbm, nx, ny):
+    p = wl.shear_layer(64, ny=max(ny, 1))
+    p.nx, p.ny = nx, ny
+    rng = np.random.default_rng(nx * 100 + ny)
+    p.rho = 1.0 + 0.05 * rng.uniform(-1, 1, (ny, nx))
+    p.ux = 0.05 * rng.uniform(-1, 1, (ny, nx))
+    p.uy = 0.05 * rng.uniform(-1, 1, (ny, nx))
+    p.T = 1.0 + 0.05 * rng.uniform(-1, 1, (ny, nx))
+    s, O = run_both(orc, lbm, p, 50)
+    _assert_fp64(fp64_errors(s, O))
+
+
+def test_delta_and_delta_star(orc, lbm):
+    p = wl.shock_interface(nx=96, ny=24, steps=150)
+    s, O = run_both(orc, lbm, p, 150)
+    g = s.moments(delta=True)[4]
+    r = O.moments(delta=True)[4]
+    sc = np.abs(r[4:]).max()
+    assert np.abs(g - r).max() <= 1e-9 * sc
+    gs = s.moments_central()
+    rs = O.moments_central()
+    assert np.abs(gs - rs).max() <= 1e-9 * np.abs(rs[4:]).max()
+
+
+def test_totals_and_state_roundtrip(orc, lbm):
+    p = wl.shear_layer(64, ny=40)
+    s, O = run_both(orc, lbm, p, 100)
+    tg, to = s.totals(), O.totals()
+    assert np.abs(tg - to).max() <= 1e-12 * np.abs(to).max()
+    fg, fo = s.get_state(), O.get_state()
+    assert np.abs(fg - fo).max() <= 1e-10 * np.abs(fo).max()
+    rows = s.get_state_rows(10, 7)
+    assert np.array_equal(rows, fg[:, 10:17, :])
+    s.set_state(fo)                                    # continue both from the oracle's state
+    s.step(20)
+    O.step(20)
+    _assert_fp64(fp64_errors(s, O))
+    assert s.step_count == 20
+
+
+def test_periodic_totals_conserved_on_gpu(lbm):
+    p = wl.shear_layer(128)
+    s = lbm.Solver.from_problem(p)
+    s.init(*p.fields())
+    t0 = s.totals()
+    s.step(500)
+    t1 = s.totals()
+    assert np.abs(t1 - t0).max() <= 1e-12 * np.abs(t0).max()
+
+
+def test_step_before_init_and_bad_n(lbm):
+    p = wl.sod(200, 2)
+    s = lbm.Solver.from_problem(p)
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(1)
+    assert e.value.code == lbm.LBM_ERR_STATE
+    s.init(*p.fields())
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(0)
+    assert e.value.code == lbm.LBM_ERR_STATE
+
+
+def test_nonfinite_state_is_reported(lbm):
+    p = wl.sod(200, 2)
+    s = lbm.Solver.from_problem(p)
+    s.init(*p.fields())
+    f = s.get_state()
+    f[3, 1, 57] = np.nan
+    s.set_state(f)
+    with pytest.raises(lbm.LbmError) as e:
+        s.moments()
+    assert e.value.code == lbm.LBM_ERR_NONFINITE
+
+
+# ------------------------------------------------------------------ FP32 deviation mode
+def _fp32_errors(s, O):
+    g, r = s.moments(), O.moments()
+    gu = np.hypot(g[1], g[2])
+    du = np.hypot(g[1] - r[1], g[2] - r[2])
+    ou = np.hypot(r[1], r[2])
+    return {
+        "rho_l1": l1_rel(g[0], r[0]), "T_l1": l1_rel(g[3], r[3]), "u_l1": float(du.sum() / ou.sum()),
+        "rho_max": max_rel(g[0], r[0]), "T_max": max_rel(g[3], r[3]),
+        "u_max": vel_max_rel(g[1], g[2], r[1], r[2]),
+    }, gu
+
+
+@pytest.mark.parametrize("name", ["shear", "sod", "shock"])
+def test_fp32_deviation_error_budget(orc, lbm, name):
+    if name == "shear":
+        p, n = wl.shear_layer(128, ny=96), 400
+    elif name == "sod":
+        p, n = wl.sod(200, 4), 1000
+    else:
+        p, n = wl.shock_interface(nx=128, ny=32, steps=300), 300
+    s, O = run_both(orc, lbm, p, n, precision=lbm.LBM_FP32_DEV)
+    e, _ = _fp32_errors(s, O)
+    for k in ("rho_l1", "T_l1", "u_l1"):
+        assert e[k] <= 1e-4, e
+    for k in ("rho_max", "T_max", "u_max"):
+        assert e[k] <= 1e-3, e
+
+
+def test_fp32_totals_drift(lbm):
+    p = wl.shear_layer(256)
+    s = lbm.Solver.from_problem(p, precision=lbm.LBM_FP32_DEV)
+    s.init(*p.fields())
+    t0 = s.totals()
+    s.step(500)
+    t1 = s.totals()
+    for k in (0, 3):                                   # mass and energy (momentum totals are ~0)
+        assert abs(t1[k] - t0[k]) <= 1e-6 * abs(t0[k])
+    assert np.abs(t1[1:3] - t0[1:3]).max() <= 1e-6 * abs(t0[0])
+
+
+# ------------------------------------------------------------------ full size, sampled
+def _patch(f_rows, y_local, x, nx):
+    """[16][5][5] neighbourhood (periodic in x) of cell (x, y_local) from a row window."""
+    out = np.zeros((16, 5, 5))
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            if dx != 0 and dy != 0:
+                continue
+            out[:, dy + 2, dx + 2] = f_rows[:, y_local + dy, (x + dx) % nx]
+    return out
+
+
+@pytest.mark.parametrize("prec", [0])
+def test_full_size_shear_layer_sampled(orc, lbm, prec):
+    """8192 x 8192 shear layer in the benchmark's launch configuration: after 3 steps,
+    64 seeded cells of step 4 are recomputed by the oracle from the GPU's step-3 state."""
+    p = wl.shear_layer(8192)
+    s = lbm.Solver.from_problem(p, precision=prec)
+    s.init(*p.fields())
+    s.step(3)
+    rng = np.random.default_rng(7)
+    ys = rng.integers(2, p.ny - 2, 64)
+    xs = rng.integers(0, p.nx, 64)
+    before = {int(y): s.get_state_rows(int(y) - 2, 5) for y in set(ys.tolist())}
+    s.step(1)
+    worst = 0.0
+    for y, x in zip(ys.tolist(), xs.tolist()):
+        want = orc.update_patch(_patch(before[y], 2, x, p.nx), p.dx, p.dt, p.gamma, p.s, p.limiter)
+        got = s.get_state_rows(y, 1)[:, 0, x]
+        worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
+    s.close()
+    assert worst <= 1e-13
