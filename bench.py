@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the D2V16 MRT flux-limiter FDLBM step on one GB300 (or N replicas).
+
+Workload: the 8192 x 8192 doubly periodic low-Mach shear layer (rho = T = 1,
+u = +-0.05 tanh layers, seeded v perturbation; gamma = 1.4, Pr = 0.71,
+dt = 1e-5), the largest grid of the benchmark set.  A step is one pass of the
+hot path: ghost fill + fused collide/convect kernel; the float64 totals
+reduction (rho, j, e) runs every 100 steps and once at the end.
+
+The headline line is the FP32 deviation mode (f stored as f - f^eq0 in float32,
+bound by HBM: 128 algorithmic bytes per cell-update); the FP64 mode (bound by the
+float64 pipe) is measured in the same run and reported under "fp64".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(weak scaling, no collective on the data path); the timing is max over ranks.
+`--impl reference` times the CPU oracle (the plain FP64 reference
+implementation of the same step) on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2V16 cell-updates/s"
+UNIT = "cell-updates/s"
+N_GRID = 8192
+BYTES_PER_CELL = {"f32": 128, "f64": 256}     # read 16 populations + write 16 populations
+# Algorithmic float64 operations per cell-update of the symmetry-factored step
+# (each add, multiply, FMA or division = one float64-pipe operation; the limiter's
+# magnitude comparisons and sign logic are exact integer operations and not counted).
+FP64_OPS_PER_CELL = 353
+TOTALS_EVERY = 100
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID, help="grid edge (default 8192)")
+    ap.add_argument("--mode", default="both", choices=["both", "f32", "f64"],
+                    help="precisions to measure (the headline line is FP32 unless --mode f64)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------------- helpers
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (identity for one process)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def pinned_like(a):
+    import numpy as np
+    import torch
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    out = t.numpy()
+    np.copyto(out, a)
+    return out, t
+
+
+# ------------------------------------------------------------------------- GPU arm
+def run_mode(lbm, p, precision, steps, warmup, device, world):
+    """Time `steps` steps (device events) and one end-to-end pass (host buffers)."""
+    import numpy as np
+    import torch
+
+    s = lbm.Solver.from_problem(p, precision=precision, device=device)
+    s.init(*p.fields())
+    s.step(warmup)
+    s.totals()
+    torch.cuda.synchronize(device)
+    stream = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize(device)
+    lbm.lbm_profile_begin(s.h, steps)
+    ev0.record(stream)
+    done = 0
+    while done < steps:
+        n = min(TOTALS_EVERY, steps - done)
+        s.step(n)
+        done += n
+        launches += 2 * n
+        s.totals()                                 # float64 reduction of rho, j, e
+        launches += 2
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    prof = lbm.lbm_profile_end(s.h)
+    barrier(world)
+    ms_local = ev0.elapsed_time(ev1)
+    ms = reduce_max(ms_local, world, torch.device("cuda", device))
+    step_kernel_ms = prof[0] / max(prof[1], 1)
+    ghost_ms = prof[2] / max(prof[3], 1)
+    totals_end = s.totals()
+    s.close()
+
+    # end to end through the C interface: host fields -> init -> steps -> moments -> host
+    rho, ux, uy, T = (pinned_like(a) for a in p.fields())
+    outs = [pinned_like(np.zeros((p.ny, p.nx))) for _ in range(4)]
+    torch.cuda.synchronize(device)
+    barrier(world)
+    t0 = time.perf_counter()
+    s = lbm.Solver.from_problem(p, precision=precision, device=device)
+    s.init(rho[0], ux[0], uy[0], T[0])
+    s.step(steps)
+    rc = lbm.lbm_moments(s.h, outs[0][0], outs[1][0], outs[2][0], outs[3][0], None)
+    t1 = time.perf_counter()
+    s.close()
+    e2e_s = reduce_max(t1 - t0, world, torch.device("cuda", device))
+    return {
+        "ms": ms, "ms_local": ms_local, "step_kernel_ms": step_kernel_ms, "ghost_ms": ghost_ms,
+        "launches": launches, "e2e_s": e2e_s, "e2e_rc": rc, "totals": [float(x) for x in totals_end],
+    }
+
+
+def cpu_baseline_run(p_full, crop: int, steps_budget_s: float = 12.0, max_steps: int = 400):
+    """The CPU oracle, as it stands, on a crop of the workload (all host cores)."""
+    import numpy as np
+    from oracle import oracle as orc
+    orc.build()
+    threads = os.cpu_count() or 1
+    orc.set_threads(threads)
+    c = min(crop, p_full.nx, p_full.ny)
+    fields = [np.ascontiguousarray(a[:c, :c]) for a in p_full.fields()]
+    O = orc.Oracle(c, c, p_full.dx, p_full.dt, p_full.gamma, p_full.s, p_full.limiter, p_full.bc)
+    O.init(*fields)
+    t0 = time.perf_counter()
+    O.step(1)
+    one = time.perf_counter() - t0
+    n = int(max(2, min(max_steps, steps_budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    O.step(n)
+    el = time.perf_counter() - t0
+    O.close()
+    return {"value": c * c * n / el, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+            "sample": f"{c}x{c} crop of the {p_full.nx}x{p_full.ny} shear layer (same dx, dt, rates), "
+                      f"{n} FP64 steps, OpenMP over cells, {el:.1f} s"}
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    from paper_1305_4736_gb300 import build, lbm, workloads as wl
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    device = local
+    torch.cuda.set_device(device)
+    if rank == 0:
+        build.build()
+    barrier(world)
+    lbm.load()
+
+    p = wl.shear_layer(args.n)
+    cells = p.nx * p.ny
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    if args.mode == "f64":
+        line = fp64_line(lbm, p, args, device, world, hbm)
+        line["fp64_headline"] = True
+        finish(line, p, args, rank, world)
+        return
+    with ClockSampler(device) as clk32:
+        r32 = run_mode(lbm, p, lbm.LBM_FP32_DEV, args.steps, args.warmup, device, world)
+    clocks = clk32.summary()
+    value = world * cells * args.steps / (r32["ms"] * 1e-3)
+    ach = BYTES_PER_CELL["f32"] * cells / (r32["step_kernel_ms"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"shear_layer_{p.nx}x{p.ny}", "mode": "FP32 deviation storage (g = f - f^eq0)",
+                   "grid": [p.nx, p.ny], "cells_per_gpu": cells, "dt": p.dt, "dx": p.dx, "gamma": p.gamma,
+                   "Pr": p.Pr, "limiter": "MC", "boundaries": "doubly periodic",
+                   "totals_every": TOTALS_EVERY, "l2": "inputs larger than L2 (4.3 GB per population buffer)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "kernel": "k_step<float,dev,MC>",
+                     "kernel_ms": r32["step_kernel_ms"], "algorithmic_bytes_per_launch": BYTES_PER_CELL["f32"] * cells,
+                     "peak_source": f"{peak_src} hbm_gbs"},
+        "e2e": {"value": world * cells * args.steps / r32["e2e_s"], "unit": UNIT,
+                "h2d_bytes_per_step": 4 * 8 * cells / args.steps, "d2h_bytes_per_step": 4 * 8 * cells / args.steps,
+                "note": "lbm_create + lbm_init (4 float64 host fields, pinned) + steps + lbm_moments "
+                        "(rho, u, v, T to host), wall clock"},
+        "gpu_launches": r32["launches"],
+        "clocks": clocks,
+        "kernel_ms": {"step": r32["step_kernel_ms"], "ghost": r32["ghost_ms"]},
+    }
+    if args.mode == "both":
+        line["fp64"] = fp64_line(lbm, p, args, device, world, hbm)
+    finish(line, p, args, rank, world)
+
+
+def fp64_line(lbm, p, args, device, world, hbm):
+    cells = p.nx * p.ny
+    k64 = max(3, args.steps // 10) if args.mode == "both" else args.steps
+    peak64 = lbm.lbm_peak_fp64(device)
+    with ClockSampler(device) as clk64:
+        r64 = run_mode(lbm, p, lbm.LBM_FP64, k64, args.warmup, device, world)
+    ops = FP64_OPS_PER_CELL * cells / (r64["step_kernel_ms"] * 1e-3)
+    peak_ops = peak64 / 2.0
+    return {
+        "metric": METRIC, "value": world * cells * k64 / (r64["ms"] * 1e-3), "unit": UNIT, "steps": k64,
+        "warmup": args.warmup, "n_gpus": world, "ms_per_step": r64["ms"] / k64, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+        "config": {"workload": f"shear_layer_{p.nx}x{p.ny}", "mode": "FP64 (f stored in float64)",
+                   "grid": [p.nx, p.ny], "l2": "inputs larger than L2 (8.6 GB per population buffer)"},
+        "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "T fp64-op/s", "frac": ops / peak_ops, "traffic": None,
+                     "kernel": "k_step<double,plain,MC>", "kernel_ms": r64["step_kernel_ms"],
+                     "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
+                     "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
+                     "hbm_frac": BYTES_PER_CELL["f64"] * cells / (r64["step_kernel_ms"] * 1e-3) / 1e9 / hbm},
+        "e2e": {"value": world * cells * k64 / r64["e2e_s"], "unit": UNIT,
+                "h2d_bytes_per_step": 4 * 8 * cells / k64, "d2h_bytes_per_step": 4 * 8 * cells / k64},
+        "gpu_launches": r64["launches"], "clocks": clk64.summary(),
+        "kernel_ms": {"step": r64["step_kernel_ms"], "ghost": r64["ghost_ms"]},
+    }
+
+
+def finish(line, p, args, rank, world):
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_run(p, 1024)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- reference arm
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_1305_4736_gb300 import workloads as wl
+
+    orc.build()
+    threads = os.cpu_count() or 1
+    orc.set_threads(threads)
+    p = wl.shear_layer(args.n)
+    crop = min(512, p.nx)
+    fields = [np.ascontiguousarray(a[:crop, :crop]) for a in p.fields()]
+    O = orc.Oracle(crop, crop, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*fields)
+    O.step(args.warmup)
+    t0 = time.perf_counter()
+    O.step(args.steps)
+    el = time.perf_counter() - t0
+    O.close()
+    value = crop * crop * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"shear_layer_{p.nx}x{p.ny}", "grid": [p.nx, p.ny],
+                   "sample": f"{crop}x{crop} crop per step", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+                         "sample": f"{crop}x{crop} crop of the {p.nx}x{p.ny} shear layer, "
+                                   f"{args.warmup}+{args.steps} FP64 steps, OpenMP over cells"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,21 @@ int lbm_set_state(lbm_ctx *ctx, const double *f);
    LBM_ERR_ARG if the window leaves [0, ny).  Synchronous. */
 int lbm_get_state_rows(lbm_ctx *ctx, int row0, int rows, double *f);
 
+/* Kernel timing for measurement.  lbm_profile_begin(ctx, max_steps) makes the next
+   lbm_step calls record a CUDA event pair around each ghost-fill and each fused-step
+   launch (up to max_steps steps; the events live on the context's stream).
+   lbm_profile_end(ctx, out) waits for them and writes out[0] = total fused-step
+   kernel time in ms, out[1] = fused-step launches, out[2] = total ghost-fill time
+   in ms, out[3] = ghost-fill launches, then stops recording.
+   LBM_ERR_STATE if lbm_profile_end is called without lbm_profile_begin. */
+int lbm_profile_begin(lbm_ctx *ctx, int max_steps);
+int lbm_profile_end(lbm_ctx *ctx, double out[4]);
+
+/* Measurement helper (not part of the method): sustained float64 FMA throughput of
+   device `device` from an FMA-chain kernel, in FLOP/s (FMA = 2), written to *flops.
+   The roofline of the float64 mode, which is bound by the float64 pipe, uses it. */
+int lbm_peak_fp64(int device, double *flops);
+
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
@@ -40,6 +41,10 @@ struct lbm_ctx {
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0;
+    // profiling (lbm_profile_begin / lbm_profile_end)
+    bool prof = false;
+    int prof_max = 0, prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev;   // 4 per step: ghost start/end, step start/end
     std::string err;
 };
 
@@ -90,7 +95,7 @@ bool invert(int n, const double *A, double *Ai)
 // (rows of Appendix A evaluated on the velocity set of Sec. II), inverted and
 // scaled by the butterfly normalisation (axis shells: S/4, X/2, Y/2, Q/4;
 // diagonal shells: all /4).
-bool build_inverse_blocks(Params &P)
+bool build_inverse_blocks(lbm::Coef<double> &P)
 {
     const double r2 = lbm::kSqrt2, d3 = lbm::kD3, d4 = lbm::kD4, w1 = lbm::kW1;
     // isotropic block: rows m1, m4, m5, m14; columns S1..S4
@@ -129,7 +134,7 @@ bool build_inverse_blocks(Params &P)
     return true;
 }
 
-void fold_rates(Params &P, const double *s, double dt)
+void fold_rates(lbm::Coef<double> &P, const double *s, double dt)
 {
     // collision columns: moment row k (1-based) relaxes at s_k; dt folded in
     for (int k = 0; k < 4; k++) {
@@ -154,9 +159,10 @@ void fold_rates(Params &P, const double *s, double dt)
 template <bool Dev>
 void host_feq(const Params &P, double rho, double ux, double uy, double T, double *f)
 {
+    const lbm::Coef<double> &C = P.cd;
     double q[NQ];
-    lbm::feq_hat_dev<double, Dev>(P, rho - P.rho0, rho * ux, rho * uy, rho * T - P.P0, 1.0 / rho, q);
-    lbm::pop_from_moments(P, q, f);
+    lbm::feq_hat_dev<double, Dev>(C, rho - C.rho0, rho * ux, rho * uy, rho * T - C.P0, 1.0 / rho, q);
+    lbm::pop_from_moments(C, q, f);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -256,43 +262,61 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     P.pitch = (int)pitch_of(nx);
     P.plane = (long long)(ny + 4) * P.pitch;
     P.limiter = limiter;
-    P.b = 2.0 / (gamma - 1.0);
-    P.inv_b = 1.0 / P.b;
     P.dt = dt;
+    lbm::Coef<double> &C = P.cd;
+    C.b = 2.0 / (gamma - 1.0);
+    C.inv_b = 1.0 / C.b;
+    C.four_inv_b = 4.0 / C.b;
+    C.two_b2 = 2.0 * (C.b + 2.0);
+    C.six_b = 6.0 + C.b;
+    C.b4 = C.b + 4.0;
     if (prec == LBM_FP32_DEV) {
-        P.rho0 = (opt && opt->rho0 > 0.0) ? opt->rho0 : 1.0;
+        C.rho0 = (opt && opt->rho0 > 0.0) ? opt->rho0 : 1.0;
         P.T0 = (opt && opt->T0 > 0.0) ? opt->T0 : 1.0;
-        P.P0 = P.rho0 * P.T0;
-        P.e0 = P.b * P.P0;
+        C.P0 = C.rho0 * P.T0;
+        C.e0 = C.b * C.P0;
+        C.P0T0 = C.P0 * P.T0;
     }
-    if (!build_inverse_blocks(P)) {
+    if (!build_inverse_blocks(C)) {
         delete c;
         return fail(nullptr, LBM_ERR_ARG, "transformation blocks are singular");
     }
-    fold_rates(P, s, dt);
+    fold_rates(C, s, dt);
     const double k8 = (s[7] == s[4]) ? 0.0 : s[7] / s[4] - 1.0;
     const double k9 = (s[8] == s[4]) ? 0.0 : s[8] / s[4] - 1.0;
     P.has_c9 = (k8 != 0.0 || k9 != 0.0) ? 1 : 0;
-    P.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
-    P.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
+    C.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
+    C.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
     // Courant number per shell: dt / (A_i dx), A_i = 1, 1/6, 1/sqrt2, sqrt2/3 (Sec. III)
     const double A[4] = {1.0, 1.0 / 6.0, 1.0 / lbm::kSqrt2, lbm::kSqrt2 / 3.0};
     for (int k = 0; k < 4; k++) {
-        P.cr[k] = dt / (A[k] * dx);
-        P.hh[k] = 0.25 * (1.0 - P.cr[k]);
+        C.cr[k] = dt / (A[k] * dx);
+        C.hh[k] = 0.25 * (1.0 - C.cr[k]);
     }
-    if (prec == LBM_FP32_DEV) host_feq<false>(P, P.rho0, 0.0, 0.0, P.T0, P.feq0);
+    // the float tables are the float64 tables rounded once
+    static_assert(sizeof(lbm::Coef<double>) == 2 * sizeof(lbm::Coef<float>), "Coef layout");
+    {
+        const double *src = reinterpret_cast<const double *>(&P.cd);
+        float *dst = reinterpret_cast<float *>(&P.cf);
+        for (size_t k = 0; k < sizeof(lbm::Coef<double>) / sizeof(double); k++) dst[k] = (float)src[k];
+    }
+    if (prec == LBM_FP32_DEV) host_feq<false>(P, C.rho0, 0.0, 0.0, P.T0, P.feq0);
     for (int e = 0; e < 4; e++) {
         lbm::EdgeDev &E = P.edge[e];
         E.kind = edges[e]->kind;
         E.uw = edges[e]->u;
         E.vw = edges[e]->v;
         E.Tw = edges[e]->T;
-        E.dTw = edges[e]->T - P.T0;
+        E.two_rho0_dTw = 2.0 * C.rho0 * (edges[e]->T - P.T0);
         if (E.kind == LBM_BC_EQUILIBRIUM) {
             if (prec == LBM_FP32_DEV) host_feq<true>(P, edges[e]->rho, edges[e]->u, edges[e]->v, edges[e]->T, E.feq);
             else host_feq<false>(P, edges[e]->rho, edges[e]->u, edges[e]->v, edges[e]->T, E.feq);
         }
+        E.uwf = (float)E.uw;
+        E.vwf = (float)E.vw;
+        E.Twf = (float)E.Tw;
+        E.two_rho0_dTwf = (float)E.two_rho0_dTw;
+        for (int q = 0; q < NQ; q++) E.feqf[q] = (float)E.feq[q];
     }
 
     // device, stream, allocator
@@ -393,10 +417,15 @@ int lbm_step(lbm_ctx *c, int n)
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     for (int s = 0; s < n; s++) {
+        cudaEvent_t *ev = nullptr;
+        if (c->prof && c->prof_used < c->prof_max) ev = &c->prof_ev[4 * c->prof_used++];
+        if (ev) cudaEventRecord(ev[0], c->stream);
         ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
+        if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
         ce = lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
+        if (ev) cudaEventRecord(ev[3], c->stream);
         c->cur ^= 1;
         c->steps++;
     }
@@ -552,6 +581,63 @@ int lbm_set_state(lbm_ctx *c, const double *f)
     return LBM_OK;
 }
 
+int lbm_profile_begin(lbm_ctx *c, int max_steps)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (max_steps < 1 || max_steps > (1 << 20)) return fail(c, LBM_ERR_ARG, "max_steps out of range");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.assign(4 * (size_t)max_steps, nullptr);
+    for (auto &e : c->prof_ev) {
+        ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaEventCreate");
+    }
+    c->prof = true;
+    c->prof_max = max_steps;
+    c->prof_used = 0;
+    return LBM_OK;
+}
+
+int lbm_profile_end(lbm_ctx *c, double out[4])
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!c->prof) return fail(c, LBM_ERR_STATE, "lbm_profile_end without lbm_profile_begin");
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "profile sync");
+    double step_ms = 0.0, ghost_ms = 0.0;
+    for (int i = 0; i < c->prof_used; i++) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, c->prof_ev[4 * i], c->prof_ev[4 * i + 1]);
+        cudaEventElapsedTime(&b, c->prof_ev[4 * i + 2], c->prof_ev[4 * i + 3]);
+        ghost_ms += a;
+        step_ms += b;
+    }
+    out[0] = step_ms;
+    out[1] = c->prof_used;
+    out[2] = ghost_ms;
+    out[3] = c->prof_used;
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof = false;
+    c->prof_used = c->prof_max = 0;
+    return LBM_OK;
+}
+
+int lbm_peak_fp64(int device, double *flops)
+{
+    if (!flops) return fail(nullptr, LBM_ERR_ARG, "flops is NULL");
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaSetDevice");
+    double v = 0.0;
+    ce = lbm::measure_fp64_fma(&v);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "fp64 peak kernel");
+    *flops = v;
+    return LBM_OK;
+}
+
 long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
@@ -561,6 +647,7 @@ void lbm_destroy(lbm_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->alloc.free) {
         if (c->aux) c->alloc.free(c->aux, c->aux_bytes, c->stream, c->alloc.user);
         if (c->stage) c->alloc.free(c->stage, c->stage_elems * sizeof(double), c->stream, c->alloc.user);

@@ -39,36 +39,49 @@ constexpr double kD4 = 3.0 / kSqrt2;         // component of shell 4
 constexpr double kW1 = 1.0 + 6.25;           // v^2 + eta^2, shell 1
 constexpr double kEta2 = 6.25;
 
+// Coefficient tables in the arithmetic type of a kernel (float tables for the
+// FP32 deviation mode, so that no float64 conversion runs per thread).
+template <typename R>
+struct Coef {
+    R b, inv_b, four_inv_b, two_b2, six_b, b4;   // b, 1/b, 4/b, 2(b+2), 6+b, b+4
+    R rho0, P0, e0, P0T0;                        // reference state (zero in FP64 mode)
+    // collision: inverse blocks with dt s_k and the butterfly normalisation
+    R cA[4][2];            // (Delta5, Delta14)          -> S'1..4
+    R cEx[4][3];           // (Delta8, Delta10, Delta12) -> X'1..4
+    R cEy[4][3];           // (Delta9, Delta11, Delta13) -> Y'1..4
+    R cB1[2][2];           // (Delta6, Delta16)          -> Q'1, Q'2
+    R cB2[2][2];           // (Delta7, Delta15)          -> Q'3, Q'4
+    // full inverse blocks with butterfly normalisation (f = M^-1 f_hat)
+    R iA[4][4], iEx[4][4], iEy[4][4], iB1[2][2], iB2[2][2];
+    // energy-flux correction of the collision (Sec. II): Delta8 += q8 P [...], Delta9 += q9 P [...]
+    // q = (s8/s5 - 1) / s8 / (2 dx)
+    R q8, q9;
+    // convection: Courant number c and h/2 = (1 - c)/4 per shell
+    R cr[4], hh[4];
+};
+
 struct EdgeDev {
     int kind;
     double uw, vw, Tw;          // wall velocity / temperature (NEQ wall)
-    double dTw;                 // Tw - T0 (reference-relative, NEQ wall)
+    double two_rho0_dTw;        // 2 rho0 (Tw - T0) (reference-relative, NEQ wall)
     double feq[NQ];             // fixed equilibrium (minus f^eq0 in deviation mode)
+    float uwf, vwf, Twf, two_rho0_dTwf;
+    float feqf[NQ];
 };
 
 struct Params {
-    int nx, ny, pitch, limiter;
+    int nx, ny, pitch, limiter, has_c9;
     long long plane;            // elements per population plane
-    double b, inv_b, dt;
-    // reference state of the deviation form (all zero in FP64 mode)
-    double rho0, T0, P0, e0;
+    double dt, T0;
     double feq0[NQ];            // reference populations f^eq(rho0, 0, 0, T0) (deviation mode)
-    // collision: inverse blocks with dt s_k and the butterfly normalisation
-    double cA[4][2];            // (Delta5, Delta14)         -> S'1..4
-    double cEx[4][3];           // (Delta8, Delta10, Delta12) -> X'1..4
-    double cEy[4][3];           // (Delta9, Delta11, Delta13) -> Y'1..4
-    double cB1[2][2];           // (Delta6, Delta16)          -> Q'1, Q'2
-    double cB2[2][2];           // (Delta7, Delta15)          -> Q'3, Q'4
-    // full inverse blocks with butterfly normalisation (f = M^-1 f_hat)
-    double iA[4][4], iEx[4][4], iEy[4][4], iB1[2][2], iB2[2][2];
-    // energy-flux correction of the collision (Sec. II): Delta8 += q8 P [...], Delta9 += q9 P [...]
-    // q = (s8/s5 - 1) / s8 / (2 dx)
-    double q8, q9;
-    int has_c9;
-    // convection: Courant number c and half-weight h/2 = (1 - c)/4 per shell
-    double cr[4], hh[4];
+    Coef<double> cd;
+    Coef<float> cf;
     EdgeDev edge[4];            // x-lo, x-hi, y-lo, y-hi
 };
+
+template <typename R> __host__ __device__ __forceinline__ const Coef<R> &coef(const Params &P);
+template <> __host__ __device__ __forceinline__ const Coef<double> &coef<double>(const Params &P) { return P.cd; }
+template <> __host__ __device__ __forceinline__ const Coef<float> &coef<float>(const Params &P) { return P.cf; }
 
 // ---------------------------------------------------------------------------
 // Shell butterflies
@@ -160,18 +173,19 @@ __host__ __device__ __forceinline__ Moments<R> moments_of(const Shells<R> &s)
 // all 16 rows.  With rho0 = P0 = T0 = e0 = 0 this is f_hat^eq itself.
 // ---------------------------------------------------------------------------
 template <typename R, bool Dev>
-__host__ __device__ __forceinline__ void feq_hat_dev(const Params &P, R drho, R jx, R jy, R dP, R ir, R *q)
+__host__ __device__ __forceinline__ void feq_hat_dev(const Coef<R> &C, R drho, R jx, R jy, R dP, R ir, R *q)
 {
-    const R b = R(P.b);
+    const R b = C.b;
     const R ux = jx * ir, uy = jy * ir;
     const R jx2 = jx * ux, jy2 = jy * uy, J2 = jx2 + jy2;
-    const R Pt = Dev ? R(P.P0) + dP : dP;                 // total pressure
-    const R et = Dev ? R(P.e0) + b * dP + J2 : b * dP + J2; // total e
+    const R Pt = Dev ? C.P0 + dP : dP;                   // total pressure
+    const R e_dev = b * dP + J2;                          // e - e0
+    const R et = Dev ? C.e0 + e_dev : e_dev;              // total e
     const R dxy = jx2 - jy2;
     q[0] = drho;
     q[1] = jx;
     q[2] = jy;
-    q[3] = b * dP + J2;
+    q[3] = e_dev;
     q[4] = R(2.0) * dP + J2;
     q[5] = dxy;
     q[6] = jx * uy;
@@ -185,29 +199,29 @@ __host__ __device__ __forceinline__ void feq_hat_dev(const Params &P, R drho, R 
     q[12] = (dxy - R(2.0) * Pt) * uy;
     const R T = Pt * ir;
     R iso;
-    if (Dev) iso = ir * (dP * (Pt + R(P.P0)) - R(P.P0 * P.T0) * drho);   // P^2/rho - P0^2/rho0
-    else     iso = Pt * T;                                               // P^2 / rho
-    q[13] = R(2.0) * (b + R(2.0)) * iso + (R(6.0) + b) * T * J2 + J2 * J2 * ir;
-    const R k = (b + R(4.0)) * Pt + J2;
+    if (Dev) iso = ir * (dP * (Pt + C.P0) - C.P0T0 * drho);   // P^2/rho - P0^2/rho0
+    else     iso = Pt * T;                                     // P^2 / rho
+    q[13] = C.two_b2 * iso + C.six_b * T * J2 + J2 * J2 * ir;
+    const R k = C.b4 * Pt + J2;
     q[14] = k * ux * uy;
     q[15] = k * dxy * ir;
 }
 
 // Populations from a full moment vector q (16 rows) with the full inverse blocks.
 template <typename R>
-__host__ __device__ __forceinline__ void pop_from_moments(const Params &P, const R *q, R *f)
+__host__ __device__ __forceinline__ void pop_from_moments(const Coef<R> &C, const R *q, R *f)
 {
     R S[4], X[4], Y[4], Q[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        S[k] = R(P.iA[k][0]) * q[0] + R(P.iA[k][1]) * q[3] + R(P.iA[k][2]) * q[4] + R(P.iA[k][3]) * q[13];
-        X[k] = R(P.iEx[k][0]) * q[1] + R(P.iEx[k][1]) * q[7] + R(P.iEx[k][2]) * q[9] + R(P.iEx[k][3]) * q[11];
-        Y[k] = R(P.iEy[k][0]) * q[2] + R(P.iEy[k][1]) * q[8] + R(P.iEy[k][2]) * q[10] + R(P.iEy[k][3]) * q[12];
+        S[k] = C.iA[k][0] * q[0] + C.iA[k][1] * q[3] + C.iA[k][2] * q[4] + C.iA[k][3] * q[13];
+        X[k] = C.iEx[k][0] * q[1] + C.iEx[k][1] * q[7] + C.iEx[k][2] * q[9] + C.iEx[k][3] * q[11];
+        Y[k] = C.iEy[k][0] * q[2] + C.iEy[k][1] * q[8] + C.iEy[k][2] * q[10] + C.iEy[k][3] * q[12];
     }
-    Q[0] = R(P.iB1[0][0]) * q[5] + R(P.iB1[0][1]) * q[15];
-    Q[1] = R(P.iB1[1][0]) * q[5] + R(P.iB1[1][1]) * q[15];
-    Q[2] = R(P.iB2[0][0]) * q[6] + R(P.iB2[0][1]) * q[14];
-    Q[3] = R(P.iB2[1][0]) * q[6] + R(P.iB2[1][1]) * q[14];
+    Q[0] = C.iB1[0][0] * q[5] + C.iB1[0][1] * q[15];
+    Q[1] = C.iB1[1][0] * q[5] + C.iB1[1][1] * q[15];
+    Q[2] = C.iB2[0][0] * q[6] + C.iB2[0][1] * q[14];
+    Q[3] = C.iB2[1][0] * q[6] + C.iB2[1][1] * q[14];
     unbutterfly_axis(S[0], X[0], Y[0], Q[0], f + 0);
     unbutterfly_axis(S[1], X[1], Y[1], Q[1], f + 4);
     unbutterfly_diag(S[2], X[2], Y[2], Q[2], f + 8);
@@ -221,8 +235,11 @@ __host__ __device__ __forceinline__ void pop_from_moments(const Params &P, const
 // with D+_J = f_{J+s} - f_J.  psi(theta) D+ is evaluated without the
 // division: for the MC limiter it equals minmod(2 D-, (D- + D+)/2, 2 D+)
 // (0 when D- D+ <= 0), for Lax-Wendroff D+, for upwind 0.  The magnitude
-// comparisons and the sign logic run on the integer pipe; they are exact.
-// `hh` is h/2 = (1 - c)/4 because mc2 returns twice the slope.
+// comparisons, the sign logic and the exact scaling by 4 (an exponent
+// increment) run on the integer pipe.  The scaling is exact for every normal
+// number; for a subnormal min(|D-|, |D+|) (below 2.2e-308 in float64) it is
+// off by that subnormal's own size.  `hh` is h/2 = (1 - c)/4 because mc2
+// returns twice the slope.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double mc2(double a, double b)
 {
@@ -231,9 +248,8 @@ __device__ __forceinline__ double mc2(double a, double b)
     const long long mask = 0x7fffffffffffffffLL;
     const long long aa = ia & mask, ab = ib & mask;
     const long long m = aa < ab ? aa : ab;
-    const double m4 = 4.0 * __longlong_as_double(m);
+    const long long im4 = m + (2LL << 52);                 // 4 |m| (exponent + 2)
     const long long id = __double_as_longlong(a + b) & mask;
-    const long long im4 = __double_as_longlong(m4);
     const long long r = im4 < id ? im4 : id;
     const bool same = ((ia ^ ib) >= 0) && (m != 0);
     return __longlong_as_double(same ? (r | (ib & ~mask)) : 0LL);
@@ -245,9 +261,8 @@ __device__ __forceinline__ float mc2(float a, float b)
     const int mask = 0x7fffffff;
     const int aa = ia & mask, ab = ib & mask;
     const int m = aa < ab ? aa : ab;
-    const float m4 = 4.0f * __int_as_float(m);
+    const int im4 = m + (2 << 23);                         // 4 |m| (exponent + 2)
     const int id = __float_as_int(a + b) & mask;
-    const int im4 = __float_as_int(m4);
     const int r = im4 < id ? im4 : id;
     const bool same = ((ia ^ ib) >= 0) && (m != 0);
     return __int_as_float(same ? (r | (ib & ~mask)) : 0);

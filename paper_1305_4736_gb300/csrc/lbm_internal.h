@@ -30,4 +30,7 @@ cudaError_t launch_pack(const Params &P, int prec, const void *f, int row0, int 
 cudaError_t launch_unpack(const Params &P, int prec, void *f, int row0, int rows, const double *in,
                           cudaStream_t st);
 
+// Sustained float64 FMA rate of the current device in FLOP/s (FMA = 2).
+cudaError_t measure_fp64_fma(double *flops);
+
 }  // namespace lbm

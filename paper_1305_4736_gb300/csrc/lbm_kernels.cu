@@ -34,6 +34,11 @@ __device__ __forceinline__ bool u_cell(int x, int y, int nx, int ny)
 }
 
 template <typename R>
+__device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+template <typename R>
 __device__ __forceinline__ void load16(const R *__restrict__ f, long long plane, long long c, R *out)
 {
 #pragma unroll
@@ -48,33 +53,33 @@ template <typename R, bool Dev>
 __device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R drho, R jx, R jy, R de,
                                         R ir, R dxux, R dyux, R dxuy, R dyuy, R *out)
 {
+    const Coef<R> &C = coef<R>(P);
     const Moments<R> M = moments_of(sh);
     const R ux = jx * ir, uy = jy * ir;
     const R J2 = jx * ux + jy * uy;
-    const R dP = (de - J2) * R(P.inv_b);
+    const R dP = (de - J2) * C.inv_b;
     R q[NQ];
-    feq_hat_dev<R, Dev>(P, drho, jx, jy, dP, ir, q);
+    feq_hat_dev<R, Dev>(C, drho, jx, jy, dP, ir, q);
     R D[NQ];
 #pragma unroll
     for (int k = 4; k < NQ; k++) D[k] = M.m[k] - q[k];
     if (P.has_c9) {
-        const R Pt = Dev ? R(P.P0) + dP : dP;
+        const R Pt = Dev ? C.P0 + dP : dP;
         const R div = dxux + dyuy, shr = dxuy + dyux;
-        const R fb = R(4.0) * R(P.inv_b);
-        D[7] += R(P.q8) * Pt * (ux * (R(4.0) * dxux - fb * div) + R(2.0) * uy * shr);
-        D[8] += R(P.q9) * Pt * (R(2.0) * ux * shr + uy * (R(4.0) * dyuy - fb * div));
+        D[7] += C.q8 * Pt * (ux * (R(4.0) * dxux - C.four_inv_b * div) + R(2.0) * uy * shr);
+        D[8] += C.q9 * Pt * (R(2.0) * ux * shr + uy * (R(4.0) * dyuy - C.four_inv_b * div));
     }
     R S[4], X[4], Y[4], Q[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        S[k] = R(P.cA[k][0]) * D[4] + R(P.cA[k][1]) * D[13];
-        X[k] = R(P.cEx[k][0]) * D[7] + R(P.cEx[k][1]) * D[9] + R(P.cEx[k][2]) * D[11];
-        Y[k] = R(P.cEy[k][0]) * D[8] + R(P.cEy[k][1]) * D[10] + R(P.cEy[k][2]) * D[12];
+        S[k] = C.cA[k][0] * D[4] + C.cA[k][1] * D[13];
+        X[k] = C.cEx[k][0] * D[7] + C.cEx[k][1] * D[9] + C.cEx[k][2] * D[11];
+        Y[k] = C.cEy[k][0] * D[8] + C.cEy[k][1] * D[10] + C.cEy[k][2] * D[12];
     }
-    Q[0] = R(P.cB1[0][0]) * D[5] + R(P.cB1[0][1]) * D[15];
-    Q[1] = R(P.cB1[1][0]) * D[5] + R(P.cB1[1][1]) * D[15];
-    Q[2] = R(P.cB2[0][0]) * D[6] + R(P.cB2[0][1]) * D[14];
-    Q[3] = R(P.cB2[1][0]) * D[6] + R(P.cB2[1][1]) * D[14];
+    Q[0] = C.cB1[0][0] * D[5] + C.cB1[0][1] * D[15];
+    Q[1] = C.cB1[1][0] * D[5] + C.cB1[1][1] * D[15];
+    Q[2] = C.cB2[0][0] * D[6] + C.cB2[0][1] * D[14];
+    Q[3] = C.cB2[1][0] * D[6] + C.cB2[1][1] * D[14];
     unbutterfly_axis(S[0], X[0], Y[0], Q[0], out + 0);
     unbutterfly_axis(S[1], X[1], Y[1], Q[1], out + 4);
     unbutterfly_diag(S[2], X[2], Y[2], Q[2], out + 8);
@@ -87,7 +92,7 @@ __device__ __forceinline__ void velocity_of(const Params &P, const R *f, R &ux, 
     const Shells<R> s = shells_of(f);
     R drho, jx, jy, de;
     conserved_of(s, drho, jx, jy, de);
-    const R rho = Dev ? R(P.rho0) + drho : drho;
+    const R rho = Dev ? coef<R>(P).rho0 + drho : drho;
     const R ir = R(1.0) / rho;
     ux = jx * ir;
     uy = jy * ir;
@@ -117,7 +122,7 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
         load16(fin, plane, c0, f);
         sh = shells_of(f);
         conserved_of(sh, drho, jx, jy, de);
-        const R rho = Dev ? R(P.rho0) + drho : drho;
+        const R rho = Dev ? coef<R>(P).rho0 + drho : drho;
         ir = R(1.0) / rho;
         su[ty + 1][tx + 1] = jx * ir;
         sv[ty + 1][tx + 1] = jy * ir;
@@ -162,23 +167,25 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
     for (int q = 0; q < NQ; q++) acc[q] = f[q] - acc[q];
 
     // limited convection: x and y projections, both from f^n (Sec. III)
+    const Coef<R> &C = coef<R>(P);
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
         const int sx = sgn_x(q), sy = sgn_y(q);
         const int shell = q >> 2;
-        const R hh = R(P.hh[shell]);
+        const R hh = C.hh[shell];
         const R *fq = fin + q * plane;
-        R tot = R(0);
+        R tx_ = R(0), ty_ = R(0);
         if (sx != 0) {
             const R fmm = fq[c0 - 2 * sx], fm = fq[c0 - sx], fp = fq[c0 + sx];
-            tot += flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+            tx_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
         }
         if (sy != 0) {
             const long long sp = (long long)sy * pitch;
             const R fmm = fq[c0 - 2 * sp], fm = fq[c0 - sp], fp = fq[c0 + sp];
-            tot += flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+            ty_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
         }
-        fout[q * plane + c0] = acc[q] - R(P.cr[shell]) * tot;
+        const R tot = (sx != 0 && sy != 0) ? tx_ + ty_ : (sx != 0 ? tx_ : ty_);
+        fout[q * plane + c0] = acc[q] - C.cr[shell] * tot;
     }
 }
 
@@ -220,6 +227,7 @@ __global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
     mx = mx < 0 ? 0 : (mx >= nx ? nx - 1 : mx);
     my = my < 0 ? 0 : (my >= ny ? ny - 1 : my);
     const EdgeDev &E = P.edge[edge];
+    const Coef<R> &C = coef<R>(P);
     const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
     if (E.kind == 0 || E.kind == 1) {                       // periodic / zero gradient
         const long long cs = (long long)(sy + OY) * P.pitch + (sx + OX);
@@ -227,7 +235,7 @@ __global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
         for (int q = 0; q < NQ; q++) f[q * plane + cg] = f[q * plane + cs];
     } else if (E.kind == 2) {                               // fixed equilibrium
 #pragma unroll
-        for (int q = 0; q < NQ; q++) f[q * plane + cg] = R(E.feq[q]);
+        for (int q = 0; q < NQ; q++) f[q * plane + cg] = pick<R>(E.feq[q], E.feqf[q]);
     } else {                                                // non-equilibrium extrapolation wall
         const long long cm = (long long)(my + OY) * P.pitch + (mx + OX);
         R g[NQ];
@@ -235,21 +243,22 @@ __global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
         const Shells<R> s = shells_of(g);
         R drho, jx, jy, de;
         conserved_of(s, drho, jx, jy, de);
-        const R rho = Dev ? R(P.rho0) + drho : drho;
+        const R rho = Dev ? C.rho0 + drho : drho;
         const R ir = R(1.0) / rho;
         const R J2 = (jx * jx + jy * jy) * ir;
-        const R dP = (de - J2) * R(P.inv_b);
+        const R dP = (de - J2) * C.inv_b;
         // ghost state: rho_g = rho_m, j_g = 2 rho_m u_w - j_m, P_g = rho_m (2 T_w - T_m)
-        const R jgx = R(2.0) * rho * R(E.uw) - jx;
-        const R jgy = R(2.0) * rho * R(E.vw) - jy;
-        const R dPg = Dev ? R(2.0 * P.rho0 * E.dTw) + R(2.0) * drho * R(E.Tw) - dP
-                          : R(2.0) * rho * R(E.Tw) - dP;
+        const R uw = pick<R>(E.uw, E.uwf), vw = pick<R>(E.vw, E.vwf), Tw = pick<R>(E.Tw, E.Twf);
+        const R jgx = R(2.0) * rho * uw - jx;
+        const R jgy = R(2.0) * rho * vw - jy;
+        const R dPg = Dev ? pick<R>(E.two_rho0_dTw, E.two_rho0_dTwf) + R(2.0) * drho * Tw - dP
+                          : R(2.0) * rho * Tw - dP;
         R qm[NQ], qg[NQ], d[NQ], fd[NQ];
-        feq_hat_dev<R, Dev>(P, drho, jx, jy, dP, ir, qm);
-        feq_hat_dev<R, Dev>(P, drho, jgx, jgy, dPg, ir, qg);
+        feq_hat_dev<R, Dev>(C, drho, jx, jy, dP, ir, qm);
+        feq_hat_dev<R, Dev>(C, drho, jgx, jgy, dPg, ir, qg);
 #pragma unroll
         for (int q = 0; q < NQ; q++) d[q] = qg[q] - qm[q];
-        pop_from_moments(P, d, fd);
+        pop_from_moments(C, d, fd);
 #pragma unroll
         for (int q = 0; q < NQ; q++) f[q * plane + cg] = g[q] + fd[q];
     }
@@ -269,11 +278,12 @@ __global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, cons
     if (i >= n) return;
     const int x = (int)(i % nx), y = row0 + (int)(i / nx);
     const double rho = fields[i], ux = fields[n + i], uy = fields[2 * n + i], T = fields[3 * n + i];
-    const double drho = rho - P.rho0;
-    const double dP = rho * T - P.P0;
+    const Coef<double> &C = P.cd;
+    const double drho = rho - C.rho0;
+    const double dP = rho * T - C.P0;
     double q[NQ], g[NQ];
-    feq_hat_dev<double, Dev>(P, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
-    pop_from_moments(P, q, g);
+    feq_hat_dev<double, Dev>(C, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
+    pop_from_moments(C, q, g);
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
 #pragma unroll
     for (int qq = 0; qq < NQ; qq++) f[qq * P.plane + c] = R(g[qq]);
@@ -288,16 +298,17 @@ __device__ __forceinline__ void moment_rows(const Params &P, const double *g, do
 {
     const Shells<double> s = shells_of(g);
     const Moments<double> M = moments_of(s);
+    const Coef<double> &C = P.cd;
     const double drho = M.m[0], jx = M.m[1], jy = M.m[2], de = M.m[3];
-    rho = Dev ? P.rho0 + drho : drho;
+    rho = Dev ? C.rho0 + drho : drho;
     ir = 1.0 / rho;
     ux = jx * ir;
     uy = jy * ir;
     const double J2 = jx * ux + jy * uy;
-    const double dP = (de - J2) * P.inv_b;
-    T = (Dev ? P.P0 + dP : dP) * ir;
+    const double dP = (de - J2) * C.inv_b;
+    T = (Dev ? C.P0 + dP : dP) * ir;
     double q[NQ];
-    feq_hat_dev<double, Dev>(P, drho, jx, jy, dP, ir, q);
+    feq_hat_dev<double, Dev>(C, drho, jx, jy, dP, ir, q);
 #pragma unroll
     for (int k = 0; k < NQ; k++) D[k] = M.m[k] - q[k];
 }
@@ -338,7 +349,7 @@ __global__ void k_moments(const __grid_constant__ Params P, const R *__restrict_
     if (dstar_o) {
         // f - f^eq = M^-1 Delta, then the rows of M* at w = v_i - u (Appendix A)
         double fn[NQ], out[NQ];
-        pop_from_moments(P, D, fn);
+        pop_from_moments(P.cd, D, fn);
 #pragma unroll
         for (int k = 0; k < NQ; k++) out[k] = 0.0;
 #pragma unroll
@@ -399,10 +410,10 @@ k_totals_partial(const __grid_constant__ Params P, const R *__restrict__ f, doub
         const Shells<double> s = shells_of(g);
         double drho, jx, jy, de;
         conserved_of(s, drho, jx, jy, de);
-        a[0] += Dev ? P.rho0 + drho : drho;
+        a[0] += Dev ? P.cd.rho0 + drho : drho;
         a[1] += jx;
         a[2] += jy;
-        a[3] += Dev ? P.e0 + de : de;
+        a[3] += Dev ? P.cd.e0 + de : de;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll

@@ -30,7 +30,7 @@ LBM_FP64, LBM_FP32_DEV = 0, 1
 
 EXPORTS = ["lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_central",
            "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count",
-           "lbm_footprint",
+           "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64",
            "lbm_last_error", "lbm_destroy"]
 
 
@@ -89,6 +89,9 @@ def load(path: str = LIB_PATH):
         lib.lbm_get_state.argtypes = [vp, _D]
         lib.lbm_set_state.argtypes = [vp, _D]
         lib.lbm_get_state_rows.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D]
+        lib.lbm_profile_begin.argtypes = [vp, ctypes.c_int]
+        lib.lbm_profile_end.argtypes = [vp, _D]
+        lib.lbm_peak_fp64.argtypes = [ctypes.c_int, _D]
         lib.lbm_step_count.argtypes = [vp]
         lib.lbm_step_count.restype = ctypes.c_longlong
         lib.lbm_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -99,7 +102,7 @@ def load(path: str = LIB_PATH):
         lib.lbm_destroy.restype = None
         for name in ("lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments",
                      "lbm_moments_central", "lbm_totals", "lbm_get_state", "lbm_set_state",
-                     "lbm_get_state_rows"):
+                     "lbm_get_state_rows", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -176,6 +179,22 @@ def lbm_get_state_rows(h, row0, rows, f):
 
 def lbm_set_state(h, f):
     _check(load().lbm_set_state(h, _p(f)), h)
+
+
+def lbm_profile_begin(h, max_steps):
+    _check(load().lbm_profile_begin(h, int(max_steps)), h)
+
+
+def lbm_profile_end(h):
+    out = np.zeros(4)
+    _check(load().lbm_profile_end(h, _p(out)), h)
+    return out
+
+
+def lbm_peak_fp64(device=0) -> float:
+    out = np.zeros(1)
+    _check(load().lbm_peak_fp64(int(device), _p(out)))
+    return float(out[0])
 
 
 def lbm_step_count(h) -> int:
