@@ -282,7 +282,7 @@ def gpu_arm(args):
                    "totals_every": TOTALS_EVERY, "l2": "inputs larger than L2 (4.3 GB per population buffer)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "kernel": "k_step<float,dev,MC>",
+                     "traffic": None, "kernel": "k_step_tma<float,dev,MC>",
                      "kernel_ms": r32["step_kernel_ms"], "algorithmic_bytes_per_launch": BYTES_PER_CELL["f32"] * cells,
                      "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * cells * args.steps / r32["e2e_s"], "unit": UNIT,
@@ -314,7 +314,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
                    "grid": [p.nx, p.ny], "l2": "inputs larger than L2 (8.6 GB per population buffer)"},
         "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T fp64-op/s", "frac": ops / peak_ops, "traffic": None,
-                     "kernel": "k_step<double,plain,MC>", "kernel_ms": r64["step_kernel_ms"],
+                     "kernel": "k_step_tma<double,plain,MC>", "kernel_ms": r64["step_kernel_ms"],
                      "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
                      "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
                      "hbm_frac": BYTES_PER_CELL["f64"] * cells / (r64["step_kernel_ms"] * 1e-3) / 1e9 / hbm},

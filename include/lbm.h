@@ -43,7 +43,8 @@ enum {
     LBM_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error, ...) */
     LBM_ERR_NONFINITE = -6,  /* a moment read-back found a non-finite value or rho <= 0 */
     LBM_ERR_STATE = -7,      /* call out of order (step before init, n <= 0, ...) */
-    LBM_ERR_TIMEOUT = -8     /* reserved: a bounded device wait ran out */
+    LBM_ERR_TIMEOUT = -8     /* a bounded device wait (tile copy) ran out in a step; reported by
+                                the next lbm_moments call */
 };
 
 /* Convection schemes of Sec. III. */
@@ -92,6 +93,9 @@ typedef struct {
     void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
+    int step_kernel;               /* 0 = automatic, 1 = plain (global-memory stencil),
+                                      2 = TMA-staged tiles (grids of at least 32 x 32);
+                                      both give identical results */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */

@@ -15,6 +15,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
 
@@ -36,8 +39,11 @@ struct lbm_ctx {
     size_t stage_elems = 0;
     double *aux = nullptr;        // totals partials (kTotalsBlocks * 4) + out (4) + flag
     size_t aux_bytes = 0;
-    int *flag = nullptr;
+    int *flag = nullptr;          // non-finite / rho <= 0 seen by the moments kernel
+    int *tma_err = nullptr;       // a tile copy wait ran out in the TMA-staged step kernel
     double *tot_out = nullptr;
+    bool use_tma = false;
+    CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0;
@@ -155,13 +161,16 @@ void fold_rates(lbm::Coef<double> &P, const double *s, double dt)
     }
 }
 
-// f^eq (or f^eq - f^eq0 in deviation mode) of a state, on the host.
+// f^eq of a state (Dev = false) or its deviation f^eq - f^eq0 from the reference
+// state (Dev = true), on the host.
 template <bool Dev>
 void host_feq(const Params &P, double rho, double ux, double uy, double T, double *f)
 {
     const lbm::Coef<double> &C = P.cd;
+    const double drho = Dev ? rho - C.rho0 : rho;
+    const double dP = Dev ? rho * T - C.P0 : rho * T;
     double q[NQ];
-    lbm::feq_hat_dev<double, Dev>(C, rho - C.rho0, rho * ux, rho * uy, rho * T - C.P0, 1.0 / rho, q);
+    lbm::feq_hat_dev<double, Dev>(C, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
     lbm::pop_from_moments(C, q, f);
 }
 
@@ -194,6 +203,39 @@ void *default_alloc(size_t bytes, void *, void *)
 void default_free(void *p, size_t, void *, void *) { cudaFree(p); }
 
 size_t pitch_of(int nx) { return (size_t)((nx + 8 + 31) / 32 * 32); }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// 3-D tile-copy descriptor of one population buffer: x = padded columns, y = rows
+// (ny + 4), z = the 16 planes; box = staged tile (x halo 4, y halo 2, all planes).
+bool make_tensor_map(CUtensorMap *tm, void *base, const Params &P, int prec)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const size_t es = prec == LBM_FP32_DEV ? sizeof(float) : sizeof(double);
+    const cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 4), (cuuint64_t)NQ};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.pitch * es, (cuuint64_t)P.plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)lbm::TmaShape<float>::SW, (cuuint32_t)lbm::TmaShape<float>::SH,
+                               (cuuint32_t)NQ};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(tm, prec == LBM_FP32_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -352,6 +394,20 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->f[1] = (char *)c->buf + c->buf_bytes / 2;
     c->tot_out = c->aux + lbm::kTotalsBlocks * 4;
     c->flag = (int *)(c->tot_out + 4);
+    c->tma_err = c->flag + 1;
+    const int want = opt ? opt->step_kernel : 0;
+    if (want < 0 || want > 2) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
+    }
+    if (want != 1 && lbm::tma_supported(P) && lbm::tma_prepare() == cudaSuccess &&
+        make_tensor_map(&c->tmap[0], c->f[0], P, prec) && make_tensor_map(&c->tmap[1], c->f[1], P, prec))
+        c->use_tma = true;
+    if (want == 2 && !c->use_tma) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_ARG, "TMA-staged step kernel unavailable for this grid or driver");
+    }
+    cudaGetLastError();
     ce = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->aux, 0, c->aux_bytes, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
@@ -423,7 +479,9 @@ int lbm_step(lbm_ctx *c, int n)
         ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
         if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
-        ce = lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream);
+        ce = c->use_tma ? lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err,
+                                               c->stream)
+                        : lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
         if (ev) cudaEventRecord(ev[3], c->stream);
         c->cur ^= 1;
@@ -469,10 +527,11 @@ static int moments_impl(lbm_ctx *c, double *rho, double *u, double *v, double *T
         ce = cudaStreamSynchronize(c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "moments");
     }
-    int flag = 0;
-    ce = cudaMemcpy(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    int flags[2] = {0, 0};
+    ce = cudaMemcpy(flags, c->flag, sizeof(flags), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "flag copy");
-    if (flag) return fail(c, LBM_ERR_NONFINITE, "a cell has a non-finite value or rho <= 0");
+    if (flags[1]) return fail(c, LBM_ERR_TIMEOUT, "a tile copy wait ran out in the step kernel");
+    if (flags[0]) return fail(c, LBM_ERR_NONFINITE, "a cell has a non-finite value or rho <= 0");
     return LBM_OK;
 }
 

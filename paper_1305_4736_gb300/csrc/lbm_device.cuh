@@ -257,15 +257,12 @@ __device__ __forceinline__ double mc2(double a, double b)
 
 __device__ __forceinline__ float mc2(float a, float b)
 {
-    const int ia = __float_as_int(a), ib = __float_as_int(b);
-    const int mask = 0x7fffffff;
-    const int aa = ia & mask, ab = ib & mask;
-    const int m = aa < ab ? aa : ab;
-    const int im4 = m + (2 << 23);                         // 4 |m| (exponent + 2)
-    const int id = __float_as_int(a + b) & mask;
-    const int r = im4 < id ? im4 : id;
-    const bool same = ((ia ^ ib) >= 0) && (m != 0);
-    return __int_as_float(same ? (r | (ib & ~mask)) : 0);
+    // t = min(|a|, |b|) with sign(a) xor sign(b): negative exactly when the
+    // one-sided differences disagree in sign, which the max with 0 turns into 0.
+    float t;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
+    const float r = fmaxf(fminf(4.0f * t, fabsf(a + b)), 0.0f);
+    return copysignf(r, b);
 }
 
 template <typename R, int Lim>
@@ -277,6 +274,47 @@ __device__ __forceinline__ R flux_diff(R fmm, R fm, R f0, R fp, R hh)
     if (Lim == 1) return d1 + R(2.0) * hh * (d2 - d1);   // Lax-Wendroff: psi = 1
     const R d0 = fm - fmm;
     return d1 + hh * (mc2(d1, d2) - mc2(d0, d1));
+}
+
+// ---------------------------------------------------------------------------
+// Collision (Eq. 3 with the energy-flux correction of Sec. II):
+//   out = dt M^-1 S (f_hat - f_hat^eq), residuals of rows 1..4 are zero.
+// ---------------------------------------------------------------------------
+template <typename R, bool Dev>
+__device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R drho, R jx, R jy, R de,
+                                        R ir, R dxux, R dyux, R dxuy, R dyuy, R *out)
+{
+    const Coef<R> &C = coef<R>(P);
+    const Moments<R> M = moments_of(sh);
+    const R ux = jx * ir, uy = jy * ir;
+    const R J2 = jx * ux + jy * uy;
+    const R dP = (de - J2) * C.inv_b;
+    R q[NQ];
+    feq_hat_dev<R, Dev>(C, drho, jx, jy, dP, ir, q);
+    R D[NQ];
+#pragma unroll
+    for (int k = 4; k < NQ; k++) D[k] = M.m[k] - q[k];
+    if (P.has_c9) {
+        const R Pt = Dev ? C.P0 + dP : dP;
+        const R div = dxux + dyuy, shr = dxuy + dyux;
+        D[7] += C.q8 * Pt * (ux * (R(4.0) * dxux - C.four_inv_b * div) + R(2.0) * uy * shr);
+        D[8] += C.q9 * Pt * (R(2.0) * ux * shr + uy * (R(4.0) * dyuy - C.four_inv_b * div));
+    }
+    R S[4], X[4], Y[4], Q[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        S[k] = C.cA[k][0] * D[4] + C.cA[k][1] * D[13];
+        X[k] = C.cEx[k][0] * D[7] + C.cEx[k][1] * D[9] + C.cEx[k][2] * D[11];
+        Y[k] = C.cEy[k][0] * D[8] + C.cEy[k][1] * D[10] + C.cEy[k][2] * D[12];
+    }
+    Q[0] = C.cB1[0][0] * D[5] + C.cB1[0][1] * D[15];
+    Q[1] = C.cB1[1][0] * D[5] + C.cB1[1][1] * D[15];
+    Q[2] = C.cB2[0][0] * D[6] + C.cB2[0][1] * D[14];
+    Q[3] = C.cB2[1][0] * D[6] + C.cB2[1][1] * D[14];
+    unbutterfly_axis(S[0], X[0], Y[0], Q[0], out + 0);
+    unbutterfly_axis(S[1], X[1], Y[1], Q[1], out + 4);
+    unbutterfly_diag(S[2], X[2], Y[2], Q[2], out + 8);
+    unbutterfly_diag(S[3], X[3], Y[3], Q[3], out + 12);
 }
 
 }  // namespace lbm

@@ -60,7 +60,7 @@ class Allocator(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("allocator", ctypes.POINTER(Allocator)),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("step_kernel", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -217,7 +217,8 @@ class Solver:
     (default: torch's current stream of `device`)."""
 
     def __init__(self, nx, ny, dx, dt, gamma, Pr, s, limiter=LBM_LIMITER_MC, bc=None,
-                 precision=LBM_FP64, rho0=1.0, T0=1.0, device=0, stream=None, use_torch_allocator=True):
+                 precision=LBM_FP64, rho0=1.0, T0=1.0, device=0, stream=None, use_torch_allocator=True,
+                 step_kernel=0):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
@@ -228,7 +229,8 @@ class Solver:
         self._stream = stream
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self._keep = []
-        opts = Options(int(precision), float(rho0), float(T0), ctypes.c_void_p(handle), None, self.device)
+        opts = Options(int(precision), float(rho0), float(T0), ctypes.c_void_p(handle), None, self.device,
+                       int(step_kernel))
         if use_torch_allocator:
             dev = self.device
 

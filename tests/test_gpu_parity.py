@@ -228,3 +228,83 @@ def test_full_size_shear_layer_sampled(orc, lbm, prec):
         worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
     s.close()
     assert worst <= 1e-13
+
+
+# ------------------------------------------------------------------ TMA-staged kernel == plain kernel
+def _state_after(lbm, p, steps, precision, kernel, limiter=None):
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter if limiter is None else limiter,
+                   p.bc, precision=precision, step_kernel=kernel)
+    s.init(*p.fields())
+    s.step(steps)
+    out = s.get_state()
+    s.close()
+    return out
+
+
+# The two kernels do the same arithmetic per value; only the compiler's multiply-add
+# contraction may differ, so they agree to round-off of the storage precision.
+ROUNDOFF = {0: 1e-13, 1: 2e-5}
+
+
+def _assert_roundoff(a, b, precision):
+    assert np.abs(a - b).max() <= ROUNDOFF[precision] * np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_tma_kernel_matches_plain_kernel(lbm, precision, limiter):
+    p = wl.shock_interface(nx=150, ny=70, steps=60)          # ragged against 32 x 32 tiles
+    a = _state_after(lbm, p, 60, precision, 1, limiter)
+    b = _state_after(lbm, p, 60, precision, 2, limiter)
+    _assert_roundoff(a, b, precision)
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_tma_kernel_each_limiter_against_oracle(orc, lbm, limiter):
+    p = wl.shock_interface(nx=150, ny=70, steps=120)
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, limiter, p.bc, step_kernel=2)
+    s.init(*p.fields())
+    s.step(120)
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, limiter, p.bc)
+    O.init(*p.fields())
+    O.step(120)
+    _assert_fp64(fp64_errors(s, O))
+    fo = O.get_state()
+    assert np.abs(s.get_state() - fo).max() <= TOL * np.abs(fo).max()
+
+
+def test_fp32_state_roundtrip_against_oracle(orc, lbm):
+    """get_state / set_state in the deviation mode return and accept f (not g)."""
+    p = wl.shock_interface(nx=96, ny=40, steps=50)
+    s, O = run_both(orc, lbm, p, 50, precision=lbm.LBM_FP32_DEV)
+    fg, fo = s.get_state(), O.get_state()
+    assert np.abs(fg - fo).max() <= 1e-4 * np.abs(fo).max()
+    s.set_state(fo)
+    assert np.abs(s.get_state() - fo).max() <= 1e-6 * np.abs(fo).max()   # float32 storage of g
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tma_kernel_matches_plain_kernel_walls(lbm, precision):
+    p = wl.shear_layer(64, ny=45)
+    p.nx, p.ny = 61, 45
+    p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:45, :61]) for a in (p.rho, p.ux, p.uy, p.T))
+    p.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
+    p.bc[3] = (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)
+    p.bc[2] = (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)
+    a = _state_after(lbm, p, 80, precision, 1)
+    b = _state_after(lbm, p, 80, precision, 2)
+    _assert_roundoff(a, b, precision)
+
+
+def test_tma_kernel_parity_with_oracle(orc, lbm):
+    p = wl.shear_layer(96, ny=66)
+    p.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_PERIODIC, 0, 0, 0, 0), (wl.BC_PERIODIC, 0, 0, 0, 0)]
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter, p.bc, step_kernel=2)
+    s.init(*p.fields())
+    s.step(300)
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*p.fields())
+    O.step(300)
+    _assert_fp64(fp64_errors(s, O))
