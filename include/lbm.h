@@ -163,6 +163,28 @@ int lbm_profile_end(lbm_ctx *ctx, double out[4]);
    The roofline of the float64 mode, which is bound by the float64 pipe, uses it. */
 int lbm_peak_fp64(int device, double *flops);
 
+/* Largest ny accepted by lbm_totals_noalloc (its scratch holds one partial per grid row). */
+#define LBM_TOTALS_NOALLOC_MAX_ROWS 16384
+
+/* Conserved totals of a population field without allocating any device memory.
+   The paper has no counterpart: this is a service for callers that cannot
+   allocate -- their device memory belongs to another allocator (a framework's
+   caching pool, a serving engine with a fixed memory plan), or they must not call
+   cudaMalloc / cudaFree, which can synchronise the whole device.
+   f: device pointer to caller-owned float64 populations, dense [16][ny][nx] (the
+   layout lbm_get_state writes), on the current device.  out: host array that
+   receives sum rho, sum j_x, sum j_y, sum e, each times dx dx (as lbm_totals).
+   stream: cudaStream_t (NULL = legacy default stream); the call waits for it.
+   Scratch: a fixed file-scope device array of (LBM_TOTALS_NOALLOC_MAX_ROWS + 1) x 4
+   doubles (512 KB), held by every GPU that loads the library until the process
+   exits.  The first call on a device looks up that array's address on the device
+   (make it before any stream capture).  All calls share the array; each overwrites
+   what it uses, so nothing needs clearing, but calls that overlap on the GPU race
+   on it and must be serialised by the caller.
+   Errors: LBM_ERR_ARG (NULL pointer, nx or ny < 1, dx <= 0, ny above
+   LBM_TOTALS_NOALLOC_MAX_ROWS), LBM_ERR_CUDA.  No cudaMalloc or cudaFree is called. */
+int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream, double out[4]);
+
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 

@@ -30,7 +30,7 @@ LBM_FP64, LBM_FP32_DEV = 0, 1
 
 EXPORTS = ["lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_central",
            "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count",
-           "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64",
+           "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64", "lbm_totals_noalloc",
            "lbm_last_error", "lbm_destroy"]
 
 
@@ -92,6 +92,9 @@ def load(path: str = LIB_PATH):
         lib.lbm_profile_begin.argtypes = [vp, ctypes.c_int]
         lib.lbm_profile_end.argtypes = [vp, _D]
         lib.lbm_peak_fp64.argtypes = [ctypes.c_int, _D]
+        lib.lbm_totals_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_void_p, _D]
+        lib.lbm_totals_noalloc.restype = ctypes.c_int
         lib.lbm_step_count.argtypes = [vp]
         lib.lbm_step_count.restype = ctypes.c_longlong
         lib.lbm_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -195,6 +198,14 @@ def lbm_peak_fp64(device=0) -> float:
     out = np.zeros(1)
     _check(load().lbm_peak_fp64(int(device), _p(out)))
     return float(out[0])
+
+
+def lbm_totals_noalloc(f_device_ptr, nx, ny, dx, stream=None):
+    """Totals of a dense [16][ny][nx] float64 device field, without device allocation."""
+    out = np.zeros(4)
+    _check(load().lbm_totals_noalloc(ctypes.c_void_p(int(f_device_ptr)), int(nx), int(ny), float(dx),
+                                     ctypes.c_void_p(int(stream or 0)), _p(out)))
+    return out
 
 
 def lbm_step_count(h) -> int:
