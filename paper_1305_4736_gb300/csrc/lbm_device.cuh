@@ -265,6 +265,11 @@ __device__ __forceinline__ float mc2(float a, float b)
     return copysignf(r, b);
 }
 
+// 1/x: correctly rounded in float64; in float32 the hardware reciprocal
+// approximation (at most 2 ulp), ample for the float32 deviation mode.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
 template <typename R, int Lim>
 __device__ __forceinline__ R flux_diff(R fmm, R fm, R f0, R fp, R hh)
 {

@@ -52,7 +52,7 @@ __device__ __forceinline__ void velocity_of(const Params &P, const R *f, R &ux, 
     R drho, jx, jy, de;
     conserved_of(s, drho, jx, jy, de);
     const R rho = Dev ? coef<R>(P).rho0 + drho : drho;
-    const R ir = R(1.0) / rho;
+    const R ir = recip(rho);
     ux = jx * ir;
     uy = jy * ir;
 }
@@ -82,7 +82,7 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
         sh = shells_of(f);
         conserved_of(sh, drho, jx, jy, de);
         const R rho = Dev ? coef<R>(P).rho0 + drho : drho;
-        ir = R(1.0) / rho;
+        ir = recip(rho);
         su[ty + 1][tx + 1] = jx * ir;
         sv[ty + 1][tx + 1] = jy * ir;
     } else if (u_cell(ix, iy, nx, ny)) {
@@ -203,7 +203,7 @@ __global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
         R drho, jx, jy, de;
         conserved_of(s, drho, jx, jy, de);
         const R rho = Dev ? C.rho0 + drho : drho;
-        const R ir = R(1.0) / rho;
+        const R ir = recip(rho);
         const R J2 = (jx * jx + jy * jy) * ir;
         const R dP = (de - J2) * C.inv_b;
         // ghost state: rho_g = rho_m, j_g = 2 rho_m u_w - j_m, P_g = rho_m (2 T_w - T_m)

@@ -8,9 +8,9 @@
 //   phase 1  flow velocity and 1/rho on the tile + 1 ring (for grad u)
 //   phase 2  per row: MRT collision with the energy-flux correction (Eq. 3,
 //            Sec. II), then the limited x and y convection of Sec. III:
-//            x slopes are shared between neighbouring lanes with warp
-//            shuffles (one warp = one tile row), y slopes slide down the
-//            thread's own column of KR rows; one global write per population.
+//            x stencils read the staged row (one warp = one tile row), y slopes
+//            slide down the thread's own column of KR rows (each slope computed
+//            once); one global write per population.
 // The arithmetic per value is that of the plain kernel; results agree with it
 // to round-off (the compiler may contract multiply-adds differently).
 #include <cuda.h>
@@ -109,7 +109,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
             R drho, jx, jy, de;
             conserved_of(sh, drho, jx, jy, de);
             const R rho = Dev ? C.rho0 + drho : drho;
-            ir = R(1.0) / rho;
+            ir = recip(rho);
             ux = jx * ir;
             uy = jy * ir;
         }
@@ -122,7 +122,6 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     // ---- phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
-    const unsigned full = 0xffffffffu;
     // sliding y-window state per y-moving population: last value, face difference, slope
     R yw[NQ], yd[NQ], ym[NQ];
 #pragma unroll
@@ -176,16 +175,11 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
             const R hh = C.hh[shell];
             R tx = R(0), tyv = R(0);
             if (sx != 0) {
+                // both slopes from the staged row (sharing the upwind slope with the
+                // neighbouring lane would cost a shuffle plus a boundary-lane fix-up)
                 const R *pr = p + q * S::PL;
-                const R fm1 = pr[-sx], fp1 = pr[sx];
-                const R d1 = f[q] - fm1, d2 = fp1 - f[q];
-                const R mJ = slope2<R, Lim>(d1, d2);
-                R mJm = sx > 0 ? __shfl_up_sync(full, mJ, 1) : __shfl_down_sync(full, mJ, 1);
-                if (sx > 0 ? lane == 0 : lane == kTmaTX - 1) {
-                    const R fm2 = pr[-2 * sx];
-                    mJm = slope2<R, Lim>(fm1 - fm2, d1);
-                }
-                tx = Lim == 2 ? d1 : d1 + hh * (mJ - mJm);
+                const R fm2 = pr[-2 * sx], fm1 = pr[-sx], fp1 = pr[sx];
+                tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, hh);
             }
             if (sy != 0) {
                 const R *pc = tile + q * S::PL + (lane + 4);
