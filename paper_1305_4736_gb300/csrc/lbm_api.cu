@@ -37,7 +37,7 @@ struct lbm_ctx {
     int cur = 0;
     double *stage = nullptr;      // staging for chunked transfers
     size_t stage_elems = 0;
-    double *aux = nullptr;        // totals partials (kTotalsBlocks * 4) + out (4) + flag
+    double *aux = nullptr;        // totals partials (kTotalsBlocks * 16) + out (4) + flags
     size_t aux_bytes = 0;
     int *flag = nullptr;          // non-finite / rho <= 0 seen by the moments kernel
     int *tma_err = nullptr;       // a tile copy wait ran out in the TMA-staged step kernel
@@ -381,7 +381,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->buf_bytes = lbm_footprint(nx, ny, prec);
     const size_t cells = (size_t)nx * ny;
     c->stage_elems = std::min<size_t>(20 * cells, std::max<size_t>(20 * (size_t)nx, (size_t)8 << 20));
-    c->aux_bytes = sizeof(double) * (lbm::kTotalsBlocks * 4 + 4) + 64;
+    c->aux_bytes = sizeof(double) * (lbm::kTotalsBlocks * NQ + 4) + 64;
     c->buf = c->alloc.alloc(c->buf_bytes, c->stream, c->alloc.user);
     c->stage = c->buf ? (double *)c->alloc.alloc(c->stage_elems * sizeof(double), c->stream, c->alloc.user) : nullptr;
     c->aux = c->stage ? (double *)c->alloc.alloc(c->aux_bytes, c->stream, c->alloc.user) : nullptr;
@@ -392,7 +392,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     }
     c->f[0] = c->buf;
     c->f[1] = (char *)c->buf + c->buf_bytes / 2;
-    c->tot_out = c->aux + lbm::kTotalsBlocks * 4;
+    c->tot_out = c->aux + lbm::kTotalsBlocks * NQ;
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
     const int want = opt ? opt->step_kernel : 0;

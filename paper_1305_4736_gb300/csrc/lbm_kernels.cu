@@ -352,60 +352,84 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Totals are linear in f: pass 1 sums every population over the cells (in a fixed
+// grid-stride order; in float32 storage, runs of 32 cells are summed in float32 and
+// flushed into float64 accumulators), pass 2 adds the block sums in a fixed order
+// and takes the conserved moments (rho, j, e) of the 16 population totals.
 template <typename R, bool Dev>
 __global__ void __launch_bounds__(kTotalsThreads)
 k_totals_partial(const __grid_constant__ Params P, const R *__restrict__ f, double *partial)
 {
-    __shared__ double red[kTotalsThreads / 32][4];
+    __shared__ double red[kTotalsThreads / 32][NQ];
     const long long n = (long long)P.nx * P.ny;
-    double a[4] = {0, 0, 0, 0};
+    double a[NQ];
+    R run[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) { a[q] = 0.0; run[q] = R(0); }
+    int cnt = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % P.nx), y = (int)(i / P.nx);
         const long long c = (long long)(y + OY) * P.pitch + (x + OX);
-        double g[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; q++) g[q] = (double)f[q * P.plane + c];
-        const Shells<double> s = shells_of(g);
-        double drho, jx, jy, de;
-        conserved_of(s, drho, jx, jy, de);
-        a[0] += Dev ? P.cd.rho0 + drho : drho;
-        a[1] += jx;
-        a[2] += jy;
-        a[3] += Dev ? P.cd.e0 + de : de;
+        for (int q = 0; q < NQ; q++) run[q] += f[q * P.plane + c];
+        if (sizeof(R) == sizeof(double) || ++cnt == 32) {
+#pragma unroll
+            for (int q = 0; q < NQ; q++) { a[q] += (double)run[q]; run[q] = R(0); }
+            cnt = 0;
+        }
     }
+#pragma unroll
+    for (int q = 0; q < NQ; q++) a[q] += (double)run[q];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const double v = warp_sum(a[k]);
-        if (lane == 0) red[w][k] = v;
+    for (int q = 0; q < NQ; q++) {
+        const double v = warp_sum(a[q]);
+        if (lane == 0) red[w][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < NQ) {
         double v = 0.0;
         for (int j = 0; j < kTotalsThreads / 32; j++) v += red[j][threadIdx.x];
-        partial[blockIdx.x * 4 + threadIdx.x] = v;
+        partial[blockIdx.x * NQ + threadIdx.x] = v;
     }
 }
 
-__global__ void k_totals_final(const double *__restrict__ partial, int nblocks, double scale, double *out)
+template <bool Dev>
+__global__ void k_totals_final(const __grid_constant__ Params P, const double *__restrict__ partial, int nblocks,
+                               double scale, double *out)
 {
-    __shared__ double red[32][4];
-    double a[4] = {0, 0, 0, 0};
+    __shared__ double red[32][NQ];
+    __shared__ double tot[NQ];
+    double a[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) a[q] = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < 4; k++) a[k] += partial[b * 4 + k];
+        for (int q = 0; q < NQ; q++) a[q] += partial[b * NQ + q];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const double v = warp_sum(a[k]);
-        if (lane == 0) red[w][k] = v;
+    for (int q = 0; q < NQ; q++) {
+        const double v = warp_sum(a[q]);
+        if (lane == 0) red[w][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < NQ) {
         double v = 0.0;
         for (int j = 0; j < (int)(blockDim.x >> 5); j++) v += red[j][threadIdx.x];
-        out[threadIdx.x] = v * scale;
+        tot[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const Shells<double> s = shells_of(tot);
+        double rho, jx, jy, e;
+        conserved_of(s, rho, jx, jy, e);
+        const double n = (double)P.nx * (double)P.ny;
+        if (Dev) { rho += n * P.cd.rho0; e += n * P.cd.e0; }
+        out[0] = rho * scale;
+        out[1] = jx * scale;
+        out[2] = jy * scale;
+        out[3] = e * scale;
     }
 }
 
@@ -499,11 +523,13 @@ cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, i
 cudaError_t launch_totals(const Params &P, int prec, const void *f, double *partial, double *out, double scale,
                           cudaStream_t st)
 {
-    if (prec == 0)
+    if (prec == 0) {
         k_totals_partial<double, false><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const double *)f, partial);
-    else
+        k_totals_final<false><<<1, 256, 0, st>>>(P, partial, kTotalsBlocks, scale, out);
+    } else {
         k_totals_partial<float, true><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const float *)f, partial);
-    k_totals_final<<<1, 256, 0, st>>>(partial, kTotalsBlocks, scale, out);
+        k_totals_final<true><<<1, 256, 0, st>>>(P, partial, kTotalsBlocks, scale, out);
+    }
     return cudaGetLastError();
 }
 

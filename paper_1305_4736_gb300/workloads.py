@@ -226,3 +226,27 @@ def serving_requests(count: int = 512, seed: int = SEED, rate_hz: float = 100.0,
         prob.steps = steps
         out.append({"id": i, "kind": kind, "arrival": t, "problem": prob, "precision": precision})
     return out
+
+
+def shock_heavy_light(nx: int = 1200, ny: int = 10, steps: int = 30000) -> Problem:
+    """Shock travelling from a heavy into a light medium (the non-equilibrium study of Sec. V):
+    domain [0, 1.2] x [0, 0.01] on 1200 x 10 cells; shocked gas (1.5, 2/3, 0, p = 7/3) left of
+    x = 0.24, heavy gas (1, 0, 0, p = 1) up to the interface at x = 0.4, light gas (0.5, 0, 0, p = 1)
+    beyond; gamma = 2; inflow (fixed shocked equilibrium) on the left, outflow (zero gradient) on
+    the right, periodic y; dt = 1e-5, s_5..7 = 5e4, others 1e5; 30000 steps (t = 0.3).
+    The paper's rounded states 0.666667 and 2.33334 are taken as the exact Rankine-Hugoniot values."""
+    gamma = 2.0
+    dx = 1.2 / nx
+    rho_s, u_s, p_s, speed = normal_shock_state(1.0, 1.0, math.sqrt(2.0), gamma)
+    x = _centres(nx, dx)[None, :] * np.ones((ny, 1))
+    rho = np.where(x < 0.24, rho_s, np.where(x < 0.4, 1.0, 0.5))
+    p = np.where(x < 0.24, p_s, 1.0)
+    ux = np.where(x < 0.24, u_s, 0.0)
+    bc = [(BC_EQUILIBRIUM, rho_s, u_s, 0.0, p_s / rho_s), (BC_ZERO_GRADIENT, 0, 0, 0, 0),
+          (BC_PERIODIC, 0, 0, 0, 0), (BC_PERIODIC, 0, 0, 0, 0)]
+    s = rates(5e4, 5e4, 1e5)
+    return Problem("shock_heavy_light", nx, ny, dx, 1e-5, gamma, 1.0, s, bc,
+                   np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.zeros((ny, nx)),
+                   np.ascontiguousarray(p / rho), steps, LIMITER_MC,
+                   {"x_shock": 0.24, "x_interface": 0.4, "shock_speed": speed,
+                    "shocked": (rho_s, u_s, p_s), "heavy": (1.0, 0.0, 1.0), "light": (0.5, 0.0, 1.0)})
