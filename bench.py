@@ -42,6 +42,10 @@ BYTES_PER_CELL = {"f32": 128, "f64": 256}     # read 16 populations + write 16 p
 # magnitude comparisons and sign logic are exact integer operations and not counted).
 FP64_OPS_PER_CELL = 353
 TOTALS_EVERY = 100
+# DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture of the
+# current kernels (profiles/k_step_tma_*_shear_layer.md: 4096^2 FP32, 2048^2 FP64, scaled by
+# the cell count); None once the kernel changes and until it is captured again.
+TRAFFIC_PER_CELL = {"f32": 126.15, "f64": 247.77}
 
 
 def parse_args(argv=None):
@@ -282,7 +286,8 @@ def gpu_arm(args):
                    "totals_every": TOTALS_EVERY, "l2": "inputs larger than L2 (4.3 GB per population buffer)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": None, "kernel": "k_step_tma<float,dev,MC>",
+                     "traffic": (TRAFFIC_PER_CELL["f32"] * cells if TRAFFIC_PER_CELL.get("f32") else None),
+                     "kernel": "k_step_tma<float,dev,MC>",
                      "kernel_ms": r32["step_kernel_ms"], "algorithmic_bytes_per_launch": BYTES_PER_CELL["f32"] * cells,
                      "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * cells * args.steps / r32["e2e_s"], "unit": UNIT,
@@ -313,7 +318,8 @@ def fp64_line(lbm, p, args, device, world, hbm):
         "config": {"workload": f"shear_layer_{p.nx}x{p.ny}", "mode": "FP64 (f stored in float64)",
                    "grid": [p.nx, p.ny], "l2": "inputs larger than L2 (8.6 GB per population buffer)"},
         "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "T fp64-op/s", "frac": ops / peak_ops, "traffic": None,
+                     "unit": "T fp64-op/s", "frac": ops / peak_ops,
+                     "traffic": (TRAFFIC_PER_CELL["f64"] * cells if TRAFFIC_PER_CELL.get("f64") else None),
                      "kernel": "k_step_tma<double,plain,MC>", "kernel_ms": r64["step_kernel_ms"],
                      "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
                      "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
