@@ -93,9 +93,11 @@ typedef struct {
     void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
-    int step_kernel;               /* 0 = automatic, 1 = plain (global-memory stencil),
-                                      2 = TMA-staged tiles (grids of at least 32 x 32);
-                                      both give identical results */
+    int step_kernel;               /* fused-step kernel: 0 = automatic (TMA-staged when the grid
+                                      allows, else plain 32 x 8), 1 = plain 32 x 8 tiles
+                                      (global-memory stencil), 2 = TMA-staged 32 x 32 tiles (grids of
+                                      at least 32 x 32), 3 = plain 32 x 4, 4 = plain 32 x 16; all
+                                      agree to round-off (see lbm_autotune) */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
@@ -162,6 +164,34 @@ int lbm_profile_end(lbm_ctx *ctx, double out[4]);
    device `device` from an FMA-chain kernel, in FLOP/s (FMA = 2), written to *flops.
    The roofline of the float64 mode, which is bound by the float64 pipe, uses it. */
 int lbm_peak_fp64(int device, double *flops);
+
+/* Pick the fastest fused-step kernel for this context's grid: times `reps` launches of
+   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles when the grid
+   allows) on the context's current state, writing the spare buffer without advancing the
+   state, and keeps the fastest for later lbm_step calls.  *choice (may be NULL) receives
+   the lbm_options.step_kernel code of the winner.  Synchronous.  Not part of the paper's
+   method: a throughput tool. */
+int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
+
+/* Batched stepping of several problems (uneven grids, any mix of precision and limiter).
+   Not part of the paper's method: a throughput tool for many small grids, whose single
+   steps are launch-bound.  The contexts must be initialised, share one device and one
+   stream, and stay alive while the batch exists.  Each step of lbm_batch_step runs, per
+   group of contexts with the same precision and limiter, one batched ghost-fill launch
+   and one fused-step launch whose persistent CTAs walk a tile list (32 x 8 tiles) across
+   the group's grids; the arithmetic per cell is that of the plain step kernel.  Pairs of
+   steps are replayed from a CUDA graph captured on the first call with n >= 2.
+   Results agree with stepping each context alone to round-off (the batched kernel reads
+   its parameters from shared memory, and the compiler may contract multiply-adds
+   differently); tiles are independent, so a grid's result does not depend on the other
+   members of its batch (bit for bit).  Contexts may also be stepped alone between batch
+   steps.  Errors: LBM_ERR_ARG (NULL, empty, mixed device or stream, a
+   context listed twice), LBM_ERR_STATE (uninitialised context, n <= 0), LBM_ERR_OOM,
+   LBM_ERR_CUDA. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out);
+int lbm_batch_step(lbm_batch *batch, int n);        /* asynchronous on the shared stream */
+void lbm_batch_destroy(lbm_batch *batch);           /* waits for the stream; NULL-safe */
 
 /* Largest ny accepted by lbm_totals_noalloc (its scratch holds one partial per grid row). */
 #define LBM_TOTALS_NOALLOC_MAX_ROWS 16384

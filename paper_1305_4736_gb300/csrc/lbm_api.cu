@@ -43,6 +43,7 @@ struct lbm_ctx {
     int *tma_err = nullptr;       // a tile copy wait ran out in the TMA-staged step kernel
     double *tot_out = nullptr;
     bool use_tma = false;
+    int plain_ty = lbm::kTY;      // tile height of the plain step kernel
     CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
     bool initialized = false;
     long long steps = 0;
@@ -396,11 +397,13 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
     const int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 2) {
+    if (want < 0 || want > 4) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
-    if (want != 1 && lbm::tma_supported(P) && lbm::tma_prepare() == cudaSuccess &&
+    if (want == 3) c->plain_ty = 4;
+    if (want == 4) c->plain_ty = 16;
+    if ((want == 0 || want == 2) && lbm::tma_supported(P) && lbm::tma_prepare() == cudaSuccess &&
         make_tensor_map(&c->tmap[0], c->f[0], P, prec) && make_tensor_map(&c->tmap[1], c->f[1], P, prec))
         c->use_tma = true;
     if (want == 2 && !c->use_tma) {
@@ -481,7 +484,7 @@ int lbm_step(lbm_ctx *c, int n)
         if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
         ce = c->use_tma ? lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err,
                                                c->stream)
-                        : lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream);
+                        : lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream, c->plain_ty);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
         if (ev) cudaEventRecord(ev[3], c->stream);
         c->cur ^= 1;
@@ -697,7 +700,228 @@ int lbm_peak_fp64(int device, double *flops)
     return LBM_OK;
 }
 
+int lbm_autotune(lbm_ctx *c, int reps, int *choice)
+{
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (reps < 1 || reps > 1000) return fail(c, LBM_ERR_ARG, "reps must be in [1, 1000]");
+    if (!c->initialized) return fail(c, LBM_ERR_STATE, "autotune before lbm_init / lbm_set_state");
+    cudaError_t ce = cudaSetDevice(c->device);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32
+    int cands[4] = {1, 3, 4, 2};
+    int ncand = 3;
+    bool tma_ok = c->use_tma;
+    if (!tma_ok && lbm::tma_supported(c->P) && lbm::tma_prepare() == cudaSuccess &&
+        make_tensor_map(&c->tmap[0], c->f[0], c->P, c->prec) && make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec))
+        tma_ok = true;
+    cudaGetLastError();
+    if (tma_ok) ncand = 4;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
+    // the candidates write the other buffer without flipping it: the state does not advance
+    ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
+    float best = 1e30f;
+    int best_c = 1;
+    for (int k = 0; k < ncand && ce == cudaSuccess; k++) {
+        auto run = [&]() {
+            const int cd = cands[k];
+            if (cd == 2)
+                return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
+            return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream,
+                                    cd == 3 ? 4 : (cd == 4 ? 16 : 8));
+        };
+        ce = run();
+        if (ce != cudaSuccess) break;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && ce == cudaSuccess; r++) ce = run();
+        cudaEventRecord(e1, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce == cudaSuccess && ms < best) { best = ms; best_c = cands[k]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "autotune");
+    c->use_tma = best_c == 2;
+    c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : 8);
+    if (choice) *choice = best_c;
+    return LBM_OK;
+}
+
 long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+}  // extern "C"
+
+struct lbm_batch {
+    struct Group {
+        int prec = 0, limiter = 0;
+        std::vector<int> members;               // indices into ctxs
+        std::vector<lbm::BatchGrid> hG;
+        void *block = nullptr;                   // device: Params[n] | BatchGrid[n] | int4[ntiles]
+        size_t bytes = 0;
+        lbm::Params *dP = nullptr;
+        lbm::BatchGrid *dG = nullptr;
+        int4 *dT = nullptr;
+        int ntiles = 0, max_ghost = 0;
+    };
+    std::vector<lbm_ctx *> ctxs;
+    std::vector<Group> groups;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaGraphExec_t exec2 = nullptr;
+    lbm_allocator alloc{};
+    int device = 0, ctas = 0;
+};
+
+namespace {
+
+cudaError_t batch_upload_cur(lbm_batch *b)
+{
+    for (auto &g : b->groups) {
+        for (size_t i = 0; i < g.members.size(); i++) g.hG[i].cur = b->ctxs[g.members[i]]->cur;
+        cudaError_t ce = cudaMemcpyAsync(g.dG, g.hG.data(), g.hG.size() * sizeof(lbm::BatchGrid),
+                                         cudaMemcpyHostToDevice, b->stream);
+        if (ce != cudaSuccess) return ce;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
+{
+    for (auto &g : b->groups) {
+        cudaError_t ce = lbm::launch_ghost_batch(g.dP, g.dG, (int)g.members.size(), g.max_ghost, g.prec, phase, st);
+        if (ce == cudaSuccess)
+            ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, b->ctas, phase, st);
+        if (ce != cudaSuccess) return ce;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return fail(nullptr, LBM_ERR_ARG, "need at least one context");
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i]) return fail(nullptr, LBM_ERR_ARG, "NULL context in batch");
+        if (ctxs[i]->device != ctxs[0]->device || ctxs[i]->stream != ctxs[0]->stream)
+            return fail(nullptr, LBM_ERR_ARG, "batched contexts must share device and stream");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return fail(nullptr, LBM_ERR_ARG, "context listed twice");
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch;
+    if (!b) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->stream = ctxs[0]->stream;
+    b->device = ctxs[0]->device;
+    b->alloc = ctxs[0]->alloc;
+    cudaError_t ce = cudaSetDevice(b->device);
+    int sms = 0;
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (ce != cudaSuccess) { delete b; return cuda_fail(nullptr, ce, "device query"); }
+    b->ctas = 4 * sms;
+    for (int i = 0; i < n; i++) {
+        const lbm_ctx *c = ctxs[i];
+        lbm_batch::Group *g = nullptr;
+        for (auto &gg : b->groups)
+            if (gg.prec == c->prec && gg.limiter == c->P.limiter) g = &gg;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->prec = c->prec;
+            g->limiter = c->P.limiter;
+        }
+        g->members.push_back(i);
+    }
+    for (auto &g : b->groups) {
+        std::vector<int4> tiles;
+        std::vector<lbm::Params> hp;
+        for (size_t k = 0; k < g.members.size(); k++) {
+            const lbm_ctx *c = b->ctxs[g.members[k]];
+            hp.push_back(c->P);
+            g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->cur, 0});
+            g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
+            for (int y = 0; y < c->P.ny; y += lbm::kTY)
+                for (int x = 0; x < c->P.nx; x += lbm::kTX) tiles.push_back(make_int4((int)k, x, y, 0));
+        }
+        g.ntiles = (int)tiles.size();
+        // sections start on 256-byte boundaries (the tile list is read as int4)
+        auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+        const size_t np = up(hp.size() * sizeof(lbm::Params)), ng = up(g.hG.size() * sizeof(lbm::BatchGrid));
+        const size_t nt = tiles.size() * sizeof(int4);
+        g.bytes = np + ng + nt;
+        g.block = b->alloc.alloc(g.bytes, b->stream, b->alloc.user);
+        if (!g.block) { cudaGetLastError(); lbm_batch_destroy(b); return fail(nullptr, LBM_ERR_OOM, "batch tables"); }
+        g.dP = (lbm::Params *)g.block;
+        g.dG = (lbm::BatchGrid *)((char *)g.block + np);
+        g.dT = (int4 *)((char *)g.block + np + ng);
+        ce = cudaMemcpyAsync(g.dP, hp.data(), hp.size() * sizeof(lbm::Params), cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(g.dG, g.hG.data(), g.hG.size() * sizeof(lbm::BatchGrid), cudaMemcpyHostToDevice,
+                                 b->stream);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(g.dT, tiles.data(), nt, cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+        if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "batch tables"); }
+    }
+    ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "capture stream"); }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int n)
+{
+    if (!b) return fail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    lbm_ctx *c0 = b->ctxs[0];
+    if (n <= 0) return fail(c0, LBM_ERR_STATE, "n must be >= 1");
+    for (lbm_ctx *c : b->ctxs)
+        if (!c->initialized) return fail(c0, LBM_ERR_STATE, "a batched context was never initialised");
+    cudaError_t ce = cudaSetDevice(b->device);
+    if (ce == cudaSuccess) ce = batch_upload_cur(b);
+    if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch");
+    if (n >= 2 && !b->exec2) {
+        // capture two steps (both buffer parities) once; replays read the tables' current contents
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            cudaError_t le = batch_launch_step(b, 0, b->cap);
+            if (le == cudaSuccess) le = batch_launch_step(b, 1, b->cap);
+            ce = cudaStreamEndCapture(b->cap, &graph);
+            if (ce == cudaSuccess) ce = le;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec2, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) { b->exec2 = nullptr; return cuda_fail(c0, ce, "batch graph"); }
+    }
+    for (int k = 0; k + 1 < n; k += 2) {
+        ce = cudaGraphLaunch(b->exec2, b->stream);
+        if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch graph launch");
+    }
+    if (n & 1) {
+        ce = batch_launch_step(b, 0, b->stream);
+        if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch step");
+        for (lbm_ctx *c : b->ctxs) c->cur ^= 1;
+    }
+    for (lbm_ctx *c : b->ctxs) c->steps += n;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->exec2) cudaGraphExecDestroy(b->exec2);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto &g : b->groups)
+        if (g.block && b->alloc.free) b->alloc.free(g.block, g.bytes, b->stream, b->alloc.user);
+    delete b;
+}
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
 

@@ -19,7 +19,21 @@ constexpr int kTotalsThreads = 256;
 cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows,
                         cudaStream_t st);
 cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
-cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st);
+// Plain fused step with tiles of 32 x ty cells (ty = 4, 8 or 16).
+cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty = kTY);
+
+// One grid of a batch: its two population buffers and which one holds the current step.
+struct BatchGrid {
+    void *buf[2];
+    int cur;
+    int pad;
+};
+// Batched ghost fill (grid index = blockIdx.y) and batched fused step over a tile list
+// (int4 {grid, x0, y0, 0}); `phase` = 0 reads buf[cur], 1 reads buf[cur ^ 1].
+cudaError_t launch_ghost_batch(const Params *Pall, const BatchGrid *G, int ngrids, int max_ghost, int prec,
+                               int phase, cudaStream_t st);
+cudaError_t launch_step_batch(const Params *Pall, const BatchGrid *G, const int4 *tiles, int ntiles, int prec,
+                              int limiter, int ctas, int phase, cudaStream_t st);
 cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, int rows,
                            double *rho, double *u, double *v, double *T, double *delta,
                            double *dstar, int *flag, cudaStream_t st);

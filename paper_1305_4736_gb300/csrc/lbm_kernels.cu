@@ -58,16 +58,16 @@ __device__ __forceinline__ void velocity_of(const Params &P, const R *f, R &ux, 
 }
 
 // ---------------------------------------------------------------------------
-// Fused step
+// Fused step (plain form): one thread per cell of a 32 x TY tile; the flow
+// velocity of the tile + 1 ring goes through shared memory, the limiter reads
+// its stencil from global memory (L1 / L2).  The tile body is shared by the
+// single-grid kernel and the batched kernel (which walks a tile work list).
 // ---------------------------------------------------------------------------
-template <typename R, bool Dev, int Lim>
-__global__ void __launch_bounds__(kTX * kTY)
-k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restrict__ fout)
+template <typename R, bool Dev, int Lim, int TY>
+__device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__ fin, R *__restrict__ fout,
+                                          int x0, int y0, R (*su)[kTX + 2], R (*sv)[kTX + 2])
 {
-    __shared__ R su[kTY + 2][kTX + 2];
-    __shared__ R sv[kTY + 2][kTX + 2];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int ix = x0 + tx, iy = y0 + ty;
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const long long plane = P.plane;
@@ -95,12 +95,12 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
     }
     // ring of the tile: bottom row, top row, left column, right column
     const int t = ty * kTX + tx;
-    if (t < 2 * (kTX + kTY)) {
+    if (t < 2 * (kTX + TY)) {
         int rx, ry, lx, ly;
         if (t < kTX) { rx = x0 + t; ry = y0 - 1; lx = t + 1; ly = 0; }
-        else if (t < 2 * kTX) { rx = x0 + t - kTX; ry = y0 + kTY; lx = t - kTX + 1; ly = kTY + 1; }
-        else if (t < 2 * kTX + kTY) { rx = x0 - 1; ry = y0 + t - 2 * kTX; lx = 0; ly = t - 2 * kTX + 1; }
-        else { rx = x0 + kTX; ry = y0 + t - 2 * kTX - kTY; lx = kTX + 1; ly = t - 2 * kTX - kTY + 1; }
+        else if (t < 2 * kTX) { rx = x0 + t - kTX; ry = y0 + TY; lx = t - kTX + 1; ly = TY + 1; }
+        else if (t < 2 * kTX + TY) { rx = x0 - 1; ry = y0 + t - 2 * kTX; lx = 0; ly = t - 2 * kTX + 1; }
+        else { rx = x0 + kTX; ry = y0 + t - 2 * kTX - TY; lx = kTX + 1; ly = t - 2 * kTX - TY + 1; }
         if (u_cell(rx, ry, nx, ny)) {
             R g[NQ];
             load16(fin, plane, (long long)(ry + OY) * pitch + (rx + OX), g);
@@ -111,40 +111,80 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
         }
     }
     __syncthreads();
-    if (!inside) return;
+    if (inside) {
+        // central differences (the 1/(2 dx) factor is folded into q8, q9)
+        const int lx = tx + 1, ly = ty + 1;
+        const R dxux = su[ly][lx + 1] - su[ly][lx - 1];
+        const R dyux = su[ly + 1][lx] - su[ly - 1][lx];
+        const R dxuy = sv[ly][lx + 1] - sv[ly][lx - 1];
+        const R dyuy = sv[ly + 1][lx] - sv[ly - 1][lx];
 
-    // central differences (the 1/(2 dx) factor is folded into q8, q9)
-    const int lx = tx + 1, ly = ty + 1;
-    const R dxux = su[ly][lx + 1] - su[ly][lx - 1];
-    const R dyux = su[ly + 1][lx] - su[ly - 1][lx];
-    const R dxuy = sv[ly][lx + 1] - sv[ly][lx - 1];
-    const R dyuy = sv[ly + 1][lx] - sv[ly - 1][lx];
-
-    R acc[NQ];
-    collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+        R acc[NQ];
+        collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
 #pragma unroll
-    for (int q = 0; q < NQ; q++) acc[q] = f[q] - acc[q];
+        for (int q = 0; q < NQ; q++) acc[q] = f[q] - acc[q];
 
-    // limited convection: x and y projections, both from f^n (Sec. III)
-    const Coef<R> &C = coef<R>(P);
+        // limited convection: x and y projections, both from f^n (Sec. III)
+        const Coef<R> &C = coef<R>(P);
 #pragma unroll
-    for (int q = 0; q < NQ; q++) {
-        const int sx = sgn_x(q), sy = sgn_y(q);
-        const int shell = q >> 2;
-        const R hh = C.hh[shell];
-        const R *fq = fin + q * plane;
-        R tx_ = R(0), ty_ = R(0);
-        if (sx != 0) {
-            const R fmm = fq[c0 - 2 * sx], fm = fq[c0 - sx], fp = fq[c0 + sx];
-            tx_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+        for (int q = 0; q < NQ; q++) {
+            const int sx = sgn_x(q), sy = sgn_y(q);
+            const int shell = q >> 2;
+            const R hh = C.hh[shell];
+            const R *fq = fin + q * plane;
+            R tx_ = R(0), ty_ = R(0);
+            if (sx != 0) {
+                const R fmm = fq[c0 - 2 * sx], fm = fq[c0 - sx], fp = fq[c0 + sx];
+                tx_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+            }
+            if (sy != 0) {
+                const long long sp = (long long)sy * pitch;
+                const R fmm = fq[c0 - 2 * sp], fm = fq[c0 - sp], fp = fq[c0 + sp];
+                ty_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+            }
+            const R tot = (sx != 0 && sy != 0) ? tx_ + ty_ : (sx != 0 ? tx_ : ty_);
+            fout[q * plane + c0] = acc[q] - C.cr[shell] * tot;
         }
-        if (sy != 0) {
-            const long long sp = (long long)sy * pitch;
-            const R fmm = fq[c0 - 2 * sp], fm = fq[c0 - sp], fp = fq[c0 + sp];
-            ty_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+    }
+}
+
+template <typename R, bool Dev, int Lim, int TY>
+__global__ void __launch_bounds__(kTX * TY)
+k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restrict__ fout)
+{
+    __shared__ R su[TY + 2][kTX + 2];
+    __shared__ R sv[TY + 2][kTX + 2];
+    step_tile<R, Dev, Lim, TY>(P, fin, fout, blockIdx.x * kTX, blockIdx.y * TY, su, sv);
+}
+
+static_assert(sizeof(Params) % sizeof(int4) == 0, "Params is copied to shared memory as int4 words");
+
+// Batched step: persistent CTAs walk a tile list spanning many grids; each tile
+// names its grid, whose parameter block is copied into shared memory when the
+// grid changes.  `phase` selects which of the two buffers is the input.
+template <typename R, bool Dev, int Lim>
+__global__ void __launch_bounds__(kTX * kTY)
+k_step_batch(const Params *__restrict__ Pall, const BatchGrid *__restrict__ G, const int4 *__restrict__ tiles,
+             int ntiles, int phase)
+{
+    __shared__ R su[kTY + 2][kTX + 2];
+    __shared__ R sv[kTY + 2][kTX + 2];
+    __shared__ __align__(16) Params Ps;
+    int cur_grid = -1;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        __syncthreads();                             // the previous tile is done with su, sv, Ps
+        if (tl.x != cur_grid) {
+            const int4 *src = reinterpret_cast<const int4 *>(Pall + tl.x);
+            int4 *dst = reinterpret_cast<int4 *>(&Ps);
+            for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kTX * kTY) dst[k] = src[k];
+            cur_grid = tl.x;
+            __syncthreads();
         }
-        const R tot = (sx != 0 && sy != 0) ? tx_ + ty_ : (sx != 0 ? tx_ : ty_);
-        fout[q * plane + c0] = acc[q] - C.cr[shell] * tot;
+        const BatchGrid g = G[tl.x];
+        const int in = g.cur ^ phase;
+        step_tile<R, Dev, Lim, kTY>(Ps, (const R *)g.buf[in], (R *)g.buf[in ^ 1], tl.y, tl.z, su, sv);
     }
 }
 
@@ -153,12 +193,11 @@ k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restric
 // y edges the interior columns (the stencil is a cross; corners are unused).
 // ---------------------------------------------------------------------------
 template <typename R, bool Dev>
-__global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
+__device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, int idx)
 {
     const int nx = P.nx, ny = P.ny;
     const long long plane = P.plane;
     const int n_x = 4 * ny, n_all = 4 * ny + 4 * nx;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_all) return;
     int edge, gx, gy, sx, sy, mx, my, n, k, along;
     if (idx < n_x) {
@@ -221,6 +260,24 @@ __global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
 #pragma unroll
         for (int q = 0; q < NQ; q++) f[q * plane + cg] = g[q] + fd[q];
     }
+}
+
+template <typename R, bool Dev>
+__global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
+{
+    ghost_cell<R, Dev>(P, f, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Batched ghost fill: blockIdx.y selects the grid of the batch.
+template <typename R, bool Dev>
+__global__ void k_ghost_batch(const Params *__restrict__ Pall, const BatchGrid *__restrict__ G, int phase)
+{
+    const int gi = blockIdx.y;
+    const Params &P = Pall[gi];
+    const int n_all = 4 * (P.nx + P.ny);
+    const BatchGrid g = G[gi];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_all; idx += gridDim.x * blockDim.x)
+        ghost_cell<R, Dev>(P, (R *)g.buf[g.cur ^ phase], idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,22 +542,59 @@ cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st)
+template <typename R, bool Dev, int TY>
+static void step_launch_ty(const Params &P, const R *a, R *b, cudaStream_t st)
 {
-    const dim3 block(kTX, kTY);
-    const dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
+    const dim3 block(kTX, TY);
+    const dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + TY - 1) / TY);
+    if (P.limiter == 0) k_step<R, Dev, 0, TY><<<grid, block, 0, st>>>(P, a, b);
+    else if (P.limiter == 1) k_step<R, Dev, 1, TY><<<grid, block, 0, st>>>(P, a, b);
+    else k_step<R, Dev, 2, TY><<<grid, block, 0, st>>>(P, a, b);
+}
+
+cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty)
+{
     if (prec == 0) {
         const double *a = (const double *)fin;
         double *b = (double *)fout;
-        if (P.limiter == 0) k_step<double, false, 0><<<grid, block, 0, st>>>(P, a, b);
-        else if (P.limiter == 1) k_step<double, false, 1><<<grid, block, 0, st>>>(P, a, b);
-        else k_step<double, false, 2><<<grid, block, 0, st>>>(P, a, b);
+        if (ty == 4) step_launch_ty<double, false, 4>(P, a, b, st);
+        else if (ty == 16) step_launch_ty<double, false, 16>(P, a, b, st);
+        else step_launch_ty<double, false, 8>(P, a, b, st);
     } else {
         const float *a = (const float *)fin;
         float *b = (float *)fout;
-        if (P.limiter == 0) k_step<float, true, 0><<<grid, block, 0, st>>>(P, a, b);
-        else if (P.limiter == 1) k_step<float, true, 1><<<grid, block, 0, st>>>(P, a, b);
-        else k_step<float, true, 2><<<grid, block, 0, st>>>(P, a, b);
+        if (ty == 4) step_launch_ty<float, true, 4>(P, a, b, st);
+        else if (ty == 16) step_launch_ty<float, true, 16>(P, a, b, st);
+        else step_launch_ty<float, true, 8>(P, a, b, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_batch(const Params *Pall, const BatchGrid *G, int ngrids, int max_ghost, int prec,
+                               int phase, cudaStream_t st)
+{
+    if (ngrids == 0) return cudaSuccess;
+    const int bx = (max_ghost + 127) / 128;
+    const dim3 grid(bx < 1 ? 1 : (bx > 64 ? 64 : bx), ngrids);
+    if (prec == 0) k_ghost_batch<double, false><<<grid, 128, 0, st>>>(Pall, G, phase);
+    else k_ghost_batch<float, true><<<grid, 128, 0, st>>>(Pall, G, phase);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(const Params *Pall, const BatchGrid *G, const int4 *tiles, int ntiles, int prec,
+                              int limiter, int ctas, int phase, cudaStream_t st)
+{
+    if (ntiles == 0) return cudaSuccess;
+    const dim3 block(kTX, kTY);
+    const int grid = ntiles < ctas ? ntiles : ctas;
+    if (prec == 0) {
+        if (limiter == 0) k_step_batch<double, false, 0><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else if (limiter == 1) k_step_batch<double, false, 1><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else k_step_batch<double, false, 2><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+    } else {
+        if (limiter == 0) k_step_batch<float, true, 0><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else if (limiter == 1) k_step_batch<float, true, 1><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else k_step_batch<float, true, 2><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
     }
     return cudaGetLastError();
 }

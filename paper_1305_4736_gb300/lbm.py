@@ -31,6 +31,7 @@ LBM_FP64, LBM_FP32_DEV = 0, 1
 EXPORTS = ["lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_central",
            "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count",
            "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64", "lbm_totals_noalloc",
+           "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy",
            "lbm_last_error", "lbm_destroy"]
 
 
@@ -95,6 +96,14 @@ def load(path: str = LIB_PATH):
         lib.lbm_totals_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_void_p, _D]
         lib.lbm_totals_noalloc.restype = ctypes.c_int
+        lib.lbm_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.lbm_autotune.restype = ctypes.c_int
+        lib.lbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+        lib.lbm_batch_create.restype = ctypes.c_int
+        lib.lbm_batch_step.argtypes = [vp, ctypes.c_int]
+        lib.lbm_batch_step.restype = ctypes.c_int
+        lib.lbm_batch_destroy.argtypes = [vp]
+        lib.lbm_batch_destroy.restype = None
         lib.lbm_step_count.argtypes = [vp]
         lib.lbm_step_count.restype = ctypes.c_longlong
         lib.lbm_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -206,6 +215,52 @@ def lbm_totals_noalloc(f_device_ptr, nx, ny, dx, stream=None):
     _check(load().lbm_totals_noalloc(ctypes.c_void_p(int(f_device_ptr)), int(nx), int(ny), float(dx),
                                      ctypes.c_void_p(int(stream or 0)), _p(out)))
     return out
+
+
+def lbm_autotune(h, reps=5) -> int:
+    choice = ctypes.c_int(0)
+    _check(load().lbm_autotune(h, int(reps), ctypes.byref(choice)), h)
+    return choice.value
+
+
+def lbm_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[ctypes.c_void_p(int(h.value if hasattr(h, "value") else h))
+                                              for h in handles])
+    out = ctypes.c_void_p()
+    _check(load().lbm_batch_create(arr, len(handles), ctypes.byref(out)))
+    return out
+
+
+def lbm_batch_step(b, n):
+    rc = load().lbm_batch_step(b, int(n))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_batch_step failed")
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
+class Batch:
+    """Several Solvers stepped together (one batched launch pair per precision/limiter group)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.b = lbm_batch_create([s.h for s in self.solvers])
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lbm_step_count(h) -> int:
@@ -321,6 +376,9 @@ class Solver:
 
     def set_state(self, f):
         lbm_set_state(self.h, np.ascontiguousarray(np.asarray(f, dtype=np.float64)))
+
+    def autotune(self, reps=5):
+        return lbm_autotune(self.h, reps)
 
     @property
     def step_count(self):

@@ -1,0 +1,122 @@
+"""Batched stepping (lbm_batch) and the kernel autotuner on the GPU.
+
+- A batch of uneven grids mixing precisions, limiters and boundary kinds gives, for every
+  problem, the state of that problem stepped alone (same per-cell arithmetic; multiply-add
+  contraction may differ, so round-off of the storage precision), over odd step counts
+  (graph replay of step pairs plus a single step) and with solo steps interleaved.
+- A grid's result does not depend on the other members of its batch (bit for bit).
+- lbm_autotune does not advance the state, and the kernel it keeps still matches the oracle.
+"""
+import numpy as np
+import pytest
+
+from _gpu_helpers import fp64_errors
+from paper_1305_4736_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1305_4736_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def _problems():
+    out = []
+    out.append((wl.sod(200, 4), 0, None))
+    out.append((wl.couette(0.5, nx=4, ny=200), 0, None))
+    out.append((wl.shock_interface(nx=70, ny=20, steps=1), 1, None))
+    out.append((wl.shear_layer(100, ny=70), 0, 1))              # Lax-Wendroff
+    out.append((wl.shock_interface(nx=45, ny=37, steps=1), 0, 2))   # upwind
+    p = wl.shear_layer(64, ny=1)
+    p.nx, p.ny = 1, 1
+    p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:1, :1]) for a in (p.rho, p.ux, p.uy, p.T))
+    out.append((p, 1, None))
+    q = wl.shear_layer(64, ny=33)
+    q.nx = 40
+    q.rho, q.ux, q.uy, q.T = (np.ascontiguousarray(a[:, :40]) for a in (q.rho, q.ux, q.uy, q.T))
+    q.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
+    out.append((q, 1, None))
+    return out
+
+
+def _solver(lbm, p, prec, lim, kernel):
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter if lim is None else lim, p.bc,
+                   precision=prec, step_kernel=kernel)
+    s.init(*p.fields())
+    return s
+
+
+ROUNDOFF = {0: 1e-13, 1: 2e-5}
+
+
+def test_batch_equals_solo_to_roundoff(lbm):
+    probs = _problems()
+    batched = [_solver(lbm, p, prec, lim, 1) for p, prec, lim in probs]
+    solo = [_solver(lbm, p, prec, lim, 1) for p, prec, lim in probs]
+    b = lbm.Batch(batched)
+    b.step(37)                       # 18 graph replays of two steps + one single step
+    batched[2].step(3)               # a solo step between batch steps
+    solo[2].step(3)
+    b.step(1)
+    b.step(20)
+    for s in solo:
+        s.step(58)
+    for (p, prec, lim), x, y in zip(probs, batched, solo):
+        assert x.step_count == y.step_count
+        a, c = x.get_state(), y.get_state()
+        assert np.abs(a - c).max() <= ROUNDOFF[prec] * np.abs(c).max(), (p.name, prec, lim)
+    b.close()
+
+
+def test_batch_member_result_independent_of_mix(lbm):
+    probs = _problems()
+    mix = [_solver(lbm, p, prec, lim, 1) for p, prec, lim in probs]
+    b = lbm.Batch(mix)
+    b.step(25)
+    for k, (p, prec, lim) in enumerate(probs):
+        alone = _solver(lbm, p, prec, lim, 1)
+        one = lbm.Batch([alone])
+        one.step(25)
+        assert np.array_equal(alone.get_state(), mix[k].get_state()), (p.name, prec, lim)
+        one.close()
+    b.close()
+
+
+def test_batch_rejects_bad_sets(lbm):
+    p = wl.sod(200, 2)
+    s = _solver(lbm, p, 0, None, 1)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([s, s])
+    t = lbm.Solver.from_problem(p)             # never initialised
+    b = lbm.Batch([s, t])
+    with pytest.raises(lbm.LbmError):
+        b.step(2)
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_keeps_state_and_parity(orc, lbm, prec):
+    p = wl.shear_layer(128, ny=96)
+    s = lbm.Solver.from_problem(p, precision=prec)
+    s.init(*p.fields())
+    s.step(10)
+    before = s.get_state()
+    choice = s.autotune(3)
+    assert choice in (1, 2, 3, 4)
+    assert np.array_equal(s.get_state(), before)
+    assert s.step_count == 10
+    s.step(90)
+    if prec == 0:
+        O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+        O.init(*p.fields())
+        O.step(100)
+        errs = fp64_errors(s, O)
+        assert max(errs.values()) <= 1e-10, errs
