@@ -58,6 +58,9 @@ def parse_args(argv=None):
     ap.add_argument("--mode", default="both", choices=["both", "f32", "f64"],
                     help="precisions to measure (the headline line is FP32 unless --mode f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=64,
+                    help="requests of the serving measurement (0 = skip)")
+    ap.add_argument("--serving-steps", type=int, default=200)
     return ap.parse_args(argv)
 
 
@@ -331,7 +334,33 @@ def fp64_line(lbm, p, args, device, world, hbm):
     }
 
 
+def serving_measure(count, steps, max_nx, max_ny, device, seed=1305):
+    """Continuous-batching serving of a seeded mixed request stream (Riemann, Couette,
+    shock-interface; FP32/FP64 50/50) against one-at-a-time FP64 solving of the same
+    requests.  Arrivals are Poisson at 1.5x the measured one-at-a-time FP64 rate."""
+    from paper_1305_4736_gb300 import serving, workloads as wl
+    be = serving.GpuBackend(device)
+    reqs = wl.serving_requests(count=count, seed=seed, rate_hz=1.0, max_nx=max_nx, max_ny=max_ny, steps=steps)
+    warm = [dict(r) for r in reqs[:2]]
+    serving.one_at_a_time(be, warm, precision=0)
+    wall64, _ = serving.one_at_a_time(be, reqs, precision=0)
+    rate64 = len(reqs) / wall64
+    reqs = wl.serving_requests(count=count, seed=seed, rate_hz=1.5 * rate64, max_nx=max_nx, max_ny=max_ny,
+                               steps=steps)
+    res, st = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=True).run(reqs)
+    _, cap = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=False).run(reqs)
+    return {"capacity_solves_per_s": cap.solves_per_s, "capacity_note": "all requests available at t = 0","requests": count, "steps_per_request": steps, "grids": f"nx 64..{max_nx}, ny 4..{max_ny} log-uniform",
+            "arrival_rate_hz": 1.5 * rate64, "solves_per_s": st.solves_per_s, "p50_s": st.p50, "p99_s": st.p99,
+            "wall_s": st.wall, "max_resident_solves": st.max_resident_solves,
+            "max_resident_gb": st.max_resident_bytes / 1e9, "cell_updates_per_s": st.cell_updates / st.wall,
+            "one_at_a_time_fp64_solves_per_s": rate64, "speedup_vs_one_at_a_time_fp64": st.solves_per_s / rate64}
+
+
 def finish(line, p, args, rank, world):
+    if rank == 0 and args.serving_requests > 0:
+        import torch
+        line["serving"] = serving_measure(args.serving_requests, args.serving_steps, 1024, 256,
+                                          torch.cuda.current_device())
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(p, 1024)
     if world > 1:
