@@ -45,7 +45,7 @@ TOTALS_EVERY = 100
 # DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture of the
 # current kernels (profiles/k_step_tma_*_shear_layer.md: 4096^2 FP32, 2048^2 FP64, scaled by
 # the cell count); None once the kernel changes and until it is captured again.
-TRAFFIC_PER_CELL = {"f32": 126.15, "f64": 247.77}
+TRAFFIC_PER_CELL = {"f32": None, "f64": None}   # dram bytes per cell from an ncu capture of the current kernels
 
 
 def parse_args(argv=None):
@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--mode", default="both", choices=["both", "f32", "f64"],
                     help="precisions to measure (the headline line is FP32 unless --mode f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step-kernel", type=int, default=0,
+                    help="lbm_options.step_kernel (0 = automatic, 1/3/4 plain, 2 TMA tiles, 5 streaming)")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests of the serving measurement (0 = skip)")
     ap.add_argument("--serving-steps", type=int, default=200)
@@ -169,12 +171,18 @@ def pinned_like(a):
 
 
 # ------------------------------------------------------------------------- GPU arm
-def run_mode(lbm, p, precision, steps, warmup, device, world):
+KERNEL_NAMES = {1: "k_step<{r},{d},MC,8>", 2: "k_step_tma<{r},{d},MC>", 3: "k_step<{r},{d},MC,4>",
+                4: "k_step<{r},{d},MC,16>", 5: "k_step_stream<{r},{d},MC>"}
+
+
+def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):
     """Time `steps` steps (device events) and one end-to-end pass (host buffers)."""
     import numpy as np
     import torch
 
-    s = lbm.Solver.from_problem(p, precision=precision, device=device)
+    s = lbm.Solver.from_problem(p, precision=precision, device=device, step_kernel=step_kernel)
+    kernel = KERNEL_NAMES[s.step_kernel].format(r="float" if precision else "double",
+                                                 d="dev" if precision else "plain")
     s.init(*p.fields())
     s.step(warmup)
     s.totals()
@@ -211,7 +219,7 @@ def run_mode(lbm, p, precision, steps, warmup, device, world):
     torch.cuda.synchronize(device)
     barrier(world)
     t0 = time.perf_counter()
-    s = lbm.Solver.from_problem(p, precision=precision, device=device)
+    s = lbm.Solver.from_problem(p, precision=precision, device=device, step_kernel=step_kernel)
     s.init(rho[0], ux[0], uy[0], T[0])
     s.step(steps)
     rc = lbm.lbm_moments(s.h, outs[0][0], outs[1][0], outs[2][0], outs[3][0], None)
@@ -221,6 +229,7 @@ def run_mode(lbm, p, precision, steps, warmup, device, world):
     return {
         "ms": ms, "ms_local": ms_local, "step_kernel_ms": step_kernel_ms, "ghost_ms": ghost_ms,
         "launches": launches, "e2e_s": e2e_s, "e2e_rc": rc, "totals": [float(x) for x in totals_end],
+        "kernel": kernel,
     }
 
 
@@ -275,7 +284,7 @@ def gpu_arm(args):
         finish(line, p, args, rank, world)
         return
     with ClockSampler(device) as clk32:
-        r32 = run_mode(lbm, p, lbm.LBM_FP32_DEV, args.steps, args.warmup, device, world)
+        r32 = run_mode(lbm, p, lbm.LBM_FP32_DEV, args.steps, args.warmup, device, world, args.step_kernel)
     clocks = clk32.summary()
     value = world * cells * args.steps / (r32["ms"] * 1e-3)
     ach = BYTES_PER_CELL["f32"] * cells / (r32["step_kernel_ms"] * 1e-3) / 1e9
@@ -290,7 +299,7 @@ def gpu_arm(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": (TRAFFIC_PER_CELL["f32"] * cells if TRAFFIC_PER_CELL.get("f32") else None),
-                     "kernel": "k_step_tma<float,dev,MC>",
+                     "kernel": r32["kernel"],
                      "kernel_ms": r32["step_kernel_ms"], "algorithmic_bytes_per_launch": BYTES_PER_CELL["f32"] * cells,
                      "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * cells * args.steps / r32["e2e_s"], "unit": UNIT,
@@ -311,7 +320,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
     k64 = max(3, args.steps // 10) if args.mode == "both" else args.steps
     peak64 = lbm.lbm_peak_fp64(device)
     with ClockSampler(device) as clk64:
-        r64 = run_mode(lbm, p, lbm.LBM_FP64, k64, args.warmup, device, world)
+        r64 = run_mode(lbm, p, lbm.LBM_FP64, k64, args.warmup, device, world, args.step_kernel)
     ops = FP64_OPS_PER_CELL * cells / (r64["step_kernel_ms"] * 1e-3)
     peak_ops = peak64 / 2.0
     return {
@@ -323,7 +332,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
         "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T fp64-op/s", "frac": ops / peak_ops,
                      "traffic": (TRAFFIC_PER_CELL["f64"] * cells if TRAFFIC_PER_CELL.get("f64") else None),
-                     "kernel": "k_step_tma<double,plain,MC>", "kernel_ms": r64["step_kernel_ms"],
+                     "kernel": r64["kernel"], "kernel_ms": r64["step_kernel_ms"],
                      "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
                      "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
                      "hbm_frac": BYTES_PER_CELL["f64"] * cells / (r64["step_kernel_ms"] * 1e-3) / 1e9 / hbm},

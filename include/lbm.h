@@ -43,7 +43,7 @@ enum {
     LBM_ERR_CUDA = -5,       /* a CUDA runtime call failed (no device, launch error, ...) */
     LBM_ERR_NONFINITE = -6,  /* a moment read-back found a non-finite value or rho <= 0 */
     LBM_ERR_STATE = -7,      /* call out of order (step before init, n <= 0, ...) */
-    LBM_ERR_TIMEOUT = -8     /* a bounded device wait (tile copy) ran out in a step; reported by
+    LBM_ERR_TIMEOUT = -8     /* a bounded device wait (TMA copy) ran out in a step; reported by
                                 the next lbm_moments call */
 };
 
@@ -96,8 +96,10 @@ typedef struct {
     int step_kernel;               /* fused-step kernel: 0 = automatic (TMA-staged when the grid
                                       allows, else plain 32 x 8), 1 = plain 32 x 8 tiles
                                       (global-memory stencil), 2 = TMA-staged 32 x 32 tiles (grids of
-                                      at least 32 x 32), 3 = plain 32 x 4, 4 = plain 32 x 16; all
-                                      agree to round-off (see lbm_autotune) */
+                                      at least 32 x 32), 3 = plain 32 x 4, 4 = plain 32 x 16,
+                                      5 = streaming (CTAs walk 256-column strips row by row
+                                      through a ring of TMA-filled row slots; grids of at least
+                                      128 columns); all agree to round-off (see lbm_autotune) */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
@@ -166,8 +168,8 @@ int lbm_profile_end(lbm_ctx *ctx, double out[4]);
 int lbm_peak_fp64(int device, double *flops);
 
 /* Pick the fastest fused-step kernel for this context's grid: times `reps` launches of
-   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles when the grid
-   allows) on the context's current state, writing the spare buffer without advancing the
+   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles and the
+   streaming kernel when the grid allows) on the context's current state, writing the spare buffer without advancing the
    state, and keeps the fastest for later lbm_step calls.  *choice (may be NULL) receives
    the lbm_options.step_kernel code of the winner.  Synchronous.  Not part of the paper's
    method: a throughput tool. */
@@ -217,6 +219,10 @@ int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream,
 
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
+
+/* The lbm_options.step_kernel code (1 .. 5) of the fused-step kernel this context runs
+   (after automatic selection or lbm_autotune); -1 for a NULL context. */
+int lbm_step_kernel(const lbm_ctx *ctx);
 
 /* Device footprint in bytes of a problem of this size and precision (both buffers). */
 size_t lbm_footprint(int nx, int ny, int precision);

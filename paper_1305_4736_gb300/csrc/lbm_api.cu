@@ -40,11 +40,13 @@ struct lbm_ctx {
     double *aux = nullptr;        // totals partials (kTotalsBlocks * 16) + out (4) + flags
     size_t aux_bytes = 0;
     int *flag = nullptr;          // non-finite / rho <= 0 seen by the moments kernel
-    int *tma_err = nullptr;       // a tile copy wait ran out in the TMA-staged step kernel
+    int *tma_err = nullptr;       // a copy wait ran out in a TMA-fed step kernel
     double *tot_out = nullptr;
     bool use_tma = false;
+    bool use_stream = false;
     int plain_ty = lbm::kTY;      // tile height of the plain step kernel
     CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
+    CUtensorMap smap[2];          // row-copy descriptors (streaming kernel)
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0;
@@ -160,6 +162,17 @@ void fold_rates(lbm::Coef<double> &P, const double *s, double dt)
         P.cB2[k][0] = dt * s[6] * P.iB2[k][0];    // m7
         P.cB2[k][1] = dt * s[14] * P.iB2[k][1];   // m15
     }
+    // the same columns ordered for shell pairs (shells 2p and 2p + 1)
+    for (int p = 0; p < 2; p++)
+        for (int e = 0; e < 2; e++) {
+            for (int j = 0; j < 2; j++) P.pA[p][j][e] = P.cA[2 * p + e][j];
+            for (int j = 0; j < 3; j++) {
+                P.pEx[p][j][e] = P.cEx[2 * p + e][j];
+                P.pEy[p][j][e] = P.cEy[2 * p + e][j];
+            }
+            P.pB1[p][e] = P.cB1[e][p];
+            P.pB2[p][e] = P.cB2[e][p];
+        }
 }
 
 // f^eq of a state (Dev = false) or its deviation f^eq - f^eq0 from the reference
@@ -219,23 +232,56 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// 3-D tile-copy descriptor of one population buffer: x = padded columns, y = rows
-// (ny + 4), z = the 16 planes; box = staged tile (x halo 4, y halo 2, all planes).
-bool make_tensor_map(CUtensorMap *tm, void *base, const Params &P, int prec)
+// 3-D copy descriptor of one population buffer: x = padded columns, y = rows
+// (ny + 4), z = the 16 planes; box = box_w x box_h x all planes (the staged tile
+// of the TMA-staged kernel, or one row slot of the streaming kernel).
+bool make_tensor_map(CUtensorMap *tm, void *base, const Params &P, int prec, int box_w, int box_h)
 {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     const size_t es = prec == LBM_FP32_DEV ? sizeof(float) : sizeof(double);
     const cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 4), (cuuint64_t)NQ};
     const cuuint64_t strides[2] = {(cuuint64_t)P.pitch * es, (cuuint64_t)P.plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)lbm::TmaShape<float>::SW, (cuuint32_t)lbm::TmaShape<float>::SH,
-                               (cuuint32_t)NQ};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)NQ};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(tm, prec == LBM_FP32_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                            3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool make_tile_maps(lbm_ctx *c)
+{
+    using S = lbm::TmaShape<float>;
+    return make_tensor_map(&c->tmap[0], c->f[0], c->P, c->prec, S::SW, S::SH) &&
+           make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec, S::SW, S::SH);
+}
+
+bool make_row_maps(lbm_ctx *c)
+{
+    using S = lbm::StreamShape<float>;
+    return make_tensor_map(&c->smap[0], c->f[0], c->P, c->prec, S::BW, 1) &&
+           make_tensor_map(&c->smap[1], c->f[1], c->P, c->prec, S::BW, 1);
+}
+
+bool stream_ready(lbm_ctx *c)
+{
+    return lbm::stream_supported(c->P) && lbm::stream_prepare() == cudaSuccess && make_row_maps(c);
+}
+
+bool tma_ready(lbm_ctx *c)
+{
+    return lbm::tma_supported(c->P) && lbm::tma_prepare() == cudaSuccess && make_tile_maps(c);
+}
+
+cudaError_t launch_fused_step(lbm_ctx *c)
+{
+    if (c->use_stream)
+        return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
+    if (c->use_tma)
+        return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
+    return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream, c->plain_ty);
 }
 
 }  // namespace
@@ -334,6 +380,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     const double A[4] = {1.0, 1.0 / 6.0, 1.0 / lbm::kSqrt2, lbm::kSqrt2 / 3.0};
     for (int k = 0; k < 4; k++) {
         C.cr[k] = dt / (A[k] * dx);
+        C.ncr[k] = -C.cr[k];
         C.hh[k] = 0.25 * (1.0 - C.cr[k]);
     }
     // the float tables are the float64 tables rounded once
@@ -397,18 +444,17 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
     const int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 4) {
+    if (want < 0 || want > 5) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
     if (want == 3) c->plain_ty = 4;
     if (want == 4) c->plain_ty = 16;
-    if ((want == 0 || want == 2) && lbm::tma_supported(P) && lbm::tma_prepare() == cudaSuccess &&
-        make_tensor_map(&c->tmap[0], c->f[0], P, prec) && make_tensor_map(&c->tmap[1], c->f[1], P, prec))
-        c->use_tma = true;
-    if (want == 2 && !c->use_tma) {
+    if (want == 5 && stream_ready(c)) c->use_stream = true;
+    if ((want == 2 || (want == 0 && !c->use_stream)) && tma_ready(c)) c->use_tma = true;
+    if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream)) {
         lbm_destroy(c);
-        return fail(nullptr, LBM_ERR_ARG, "TMA-staged step kernel unavailable for this grid or driver");
+        return fail(nullptr, LBM_ERR_ARG, "requested step kernel unavailable for this grid or driver");
     }
     cudaGetLastError();
     ce = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
@@ -482,9 +528,7 @@ int lbm_step(lbm_ctx *c, int n)
         ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
         if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
-        ce = c->use_tma ? lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err,
-                                               c->stream)
-                        : lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream, c->plain_ty);
+        ce = launch_fused_step(c);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
         if (ev) cudaEventRecord(ev[3], c->stream);
         c->cur ^= 1;
@@ -533,7 +577,7 @@ static int moments_impl(lbm_ctx *c, double *rho, double *u, double *v, double *T
     int flags[2] = {0, 0};
     ce = cudaMemcpy(flags, c->flag, sizeof(flags), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "flag copy");
-    if (flags[1]) return fail(c, LBM_ERR_TIMEOUT, "a tile copy wait ran out in the step kernel");
+    if (flags[1]) return fail(c, LBM_ERR_TIMEOUT, "a copy wait ran out in the step kernel");
     if (flags[0]) return fail(c, LBM_ERR_NONFINITE, "a cell has a non-finite value or rho <= 0");
     return LBM_OK;
 }
@@ -707,15 +751,15 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "autotune before lbm_init / lbm_set_state");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
-    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32
-    int cands[4] = {1, 3, 4, 2};
+    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32, 5 = streaming
+    int cands[5] = {1, 3, 4, 0, 0};
     int ncand = 3;
-    bool tma_ok = c->use_tma;
-    if (!tma_ok && lbm::tma_supported(c->P) && lbm::tma_prepare() == cudaSuccess &&
-        make_tensor_map(&c->tmap[0], c->f[0], c->P, c->prec) && make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec))
-        tma_ok = true;
+    const bool tma_ok = c->use_tma || tma_ready(c);
     cudaGetLastError();
-    if (tma_ok) ncand = 4;
+    const bool stream_ok = c->use_stream || stream_ready(c);
+    cudaGetLastError();
+    if (tma_ok) cands[ncand++] = 2;
+    if (stream_ok) cands[ncand++] = 5;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
@@ -726,6 +770,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     for (int k = 0; k < ncand && ce == cudaSuccess; k++) {
         auto run = [&]() {
             const int cd = cands[k];
+            if (cd == 5)
+                return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err,
+                                               c->stream);
             if (cd == 2)
                 return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
             return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream,
@@ -745,12 +792,21 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "autotune");
     c->use_tma = best_c == 2;
+    c->use_stream = best_c == 5;
     c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : 8);
     if (choice) *choice = best_c;
     return LBM_OK;
 }
 
 long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+int lbm_step_kernel(const lbm_ctx *c)
+{
+    if (!c) return -1;
+    if (c->use_stream) return 5;
+    if (c->use_tma) return 2;
+    return c->plain_ty == 4 ? 3 : (c->plain_ty == 16 ? 4 : 1);
+}
 
 }  // extern "C"
 

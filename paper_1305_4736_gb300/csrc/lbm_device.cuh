@@ -58,6 +58,10 @@ struct Coef {
     R q8, q9;
     // convection: Courant number c and h/2 = (1 - c)/4 per shell
     R cr[4], hh[4];
+    // the collision blocks re-ordered for shell pairs (float32 pair arithmetic): element e of
+    // pair p belongs to shell 2p + e; e.g. pEx[p][j] = (cEx[2p][j], cEx[2p+1][j])
+    R pA[2][2][2], pEx[2][3][2], pEy[2][3][2], pB1[2][2], pB2[2][2];
+    R ncr[4];              // -cr
 };
 
 struct EdgeDev {
@@ -82,6 +86,26 @@ struct Params {
 template <typename R> __host__ __device__ __forceinline__ const Coef<R> &coef(const Params &P);
 template <> __host__ __device__ __forceinline__ const Coef<double> &coef<double>(const Params &P) { return P.cd; }
 template <> __host__ __device__ __forceinline__ const Coef<float> &coef<float>(const Params &P) { return P.cf; }
+
+// ---------------------------------------------------------------------------
+// Packed float32 pairs (f32x2 arithmetic of sm_100 and later).  Every operation
+// rounds each lane once, as the scalar operation does.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
 
 // ---------------------------------------------------------------------------
 // Shell butterflies
@@ -320,6 +344,149 @@ __device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R 
     unbutterfly_axis(S[1], X[1], Y[1], Q[1], out + 4);
     unbutterfly_diag(S[2], X[2], Y[2], Q[2], out + 8);
     unbutterfly_diag(S[3], X[3], Y[3], Q[3], out + 12);
+}
+
+// ---------------------------------------------------------------------------
+// Float32 collision on population pairs.  Pair pr holds populations (q, q+4)
+// with q = pr for pr < 4 (axis shells 1 and 2) and q = pr + 4 for pr >= 4
+// (diagonal shells 3 and 4): the two shells of a pair have the same butterfly,
+// so shells, moments, the inverse blocks and the inverse butterflies run as
+// f32x2 operations.  Same formulas as shells_of / conserved_of / collide; only
+// the summation order of some moment rows differs.
+// ---------------------------------------------------------------------------
+struct Shells2 { float2 S[2], X[2], Y[2], Q[2]; };   // [0]: shells 1, 2; [1]: shells 3, 4
+
+__device__ __forceinline__ Shells2 shells2_of(const float2 *fp)
+{
+    Shells2 s;
+    {
+        const float2 a = add2(fp[0], fp[2]), b = add2(fp[1], fp[3]);
+        s.S[0] = add2(a, b);
+        s.Q[0] = sub2(a, b);
+        s.X[0] = sub2(fp[0], fp[2]);
+        s.Y[0] = sub2(fp[1], fp[3]);
+    }
+    {
+        const float2 a = add2(fp[4], fp[6]), b = add2(fp[5], fp[7]);
+        const float2 c = sub2(fp[4], fp[6]), d = sub2(fp[5], fp[7]);
+        s.S[1] = add2(a, b);
+        s.Q[1] = sub2(a, b);
+        s.X[1] = sub2(c, d);
+        s.Y[1] = add2(c, d);
+    }
+    return s;
+}
+
+__device__ __forceinline__ void conserved2_of(const Shells2 &s, float &rho, float &jx, float &jy, float &e)
+{
+    const float2 r = add2(s.S[0], s.S[1]);
+    rho = r.x + r.y;
+    jx = fmaf(float(kD4), s.X[1].y, fmaf(float(kD3), s.X[1].x, fmaf(6.0f, s.X[0].y, s.X[0].x)));
+    jy = fmaf(float(kD4), s.Y[1].y, fmaf(float(kD3), s.Y[1].x, fmaf(6.0f, s.Y[0].y, s.Y[0].x)));
+    const float2 w = fma2(f2(float(kW1), 36.0f), s.S[0], mul2(f2(4.0f, 9.0f), s.S[1]));
+    e = w.x + w.y;
+}
+
+__device__ __forceinline__ float2 bc2(float v) { return f2(v, v); }
+
+__host__ __device__ __forceinline__ constexpr int pair_q(int pr) { return pr < 4 ? pr : pr + 4; }   // first member
+
+// Flow velocity and 1/rho of the cell whose population q is at p[q * stride].
+template <typename R, bool Dev>
+__device__ __forceinline__ void flow_at(const Coef<R> &C, const R *p, int stride, R &u, R &v, R &ir)
+{
+    R drho, jx, jy, de;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        float2 fp[8];
+#pragma unroll
+        for (int pr = 0; pr < 8; pr++) fp[pr] = f2(p[pair_q(pr) * stride], p[(pair_q(pr) + 4) * stride]);
+        conserved2_of(shells2_of(fp), drho, jx, jy, de);
+    } else {
+        R g[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) g[q] = p[q * stride];
+        conserved_of(shells_of(g), drho, jx, jy, de);
+    }
+    const R rho = Dev ? C.rho0 + drho : drho;
+    ir = recip(rho);
+    u = jx * ir;
+    v = jy * ir;
+}
+
+// Inverse butterflies of a shell pair: acc[k] = (p_k of the first shell, p_k of the second).
+__device__ __forceinline__ void unbutterfly2_axis(float2 S, float2 X, float2 Y, float2 Q, float2 *acc)
+{
+    const float2 a = add2(S, Q), b = sub2(S, Q);
+    acc[0] = add2(a, X);
+    acc[2] = sub2(a, X);
+    acc[1] = add2(b, Y);
+    acc[3] = sub2(b, Y);
+}
+
+__device__ __forceinline__ void unbutterfly2_diag(float2 S, float2 X, float2 Y, float2 Q, float2 *acc)
+{
+    const float2 a = add2(S, Q), b = sub2(S, Q), c = add2(X, Y), d = sub2(X, Y);
+    acc[0] = add2(a, c);
+    acc[2] = sub2(a, c);
+    acc[1] = sub2(b, d);
+    acc[3] = add2(b, d);
+}
+
+// acc[pr] = collision term of pair pr (dt M^-1 S (f_hat - f_hat^eq), Eq. 3 with the
+// energy-flux correction of Sec. II).
+template <bool Dev>
+__device__ __forceinline__ void collide2(const Params &P, const Shells2 &sh, float drho, float jx, float jy,
+                                         float de, float ir, float dxux, float dyux, float dxuy, float dyuy,
+                                         float2 *acc)
+{
+    const Coef<float> &C = P.cf;
+    const float S0 = sh.S[0].x, X0 = sh.X[0].x, X1 = sh.X[0].y, Y0 = sh.Y[0].x, Y1 = sh.Y[0].y;
+    const float Q0 = sh.Q[0].x, Q1 = sh.Q[0].y, Q2 = sh.Q[1].x, Q3 = sh.Q[1].y;
+    // rows 5..16 of Appendix A
+    const float m4 = fmaf(-float(kEta2), S0, de);
+    const float2 t13 = fma2(f2(float(kW1), 1296.0f), sh.S[0], mul2(f2(16.0f, 81.0f), sh.S[1]));
+    const float m13 = t13.x + t13.y;
+    const float2 c8 = f2(float(4.0 * kSqrt2), float(27.0 / kSqrt2));
+    const float2 t8x = fma2(f2(float(kW1), 216.0f), sh.X[0], mul2(c8, sh.X[1]));
+    const float2 t8y = fma2(f2(float(kW1), 216.0f), sh.Y[0], mul2(c8, sh.Y[1]));
+    const float x8 = t8x.x + t8x.y, y8 = t8y.x + t8y.y;
+    const float m9 = fmaf(-float(kEta2), X0, x8), m10 = fmaf(-float(kEta2), Y0, y8);
+    const float m11 = fmaf(216.0f, X1, X0), m12 = -fmaf(216.0f, Y1, Y0);
+    const float m5 = fmaf(36.0f, Q1, Q0), m15 = fmaf(1296.0f, Q1, float(kW1) * Q0);
+    const float m6 = fmaf(4.5f, Q3, 2.0f * Q2), m14 = fmaf(40.5f, Q3, 8.0f * Q2);
+
+    const float ux = jx * ir, uy = jy * ir;
+    const float J2 = fmaf(jx, ux, jy * uy);
+    const float dP = (de - J2) * C.inv_b;
+    float q[NQ];
+    feq_hat_dev<float, Dev>(C, drho, jx, jy, dP, ir, q);
+    const float2 D4_13 = sub2(f2(m4, m13), f2(q[4], q[13]));
+    float2 D7_8 = sub2(f2(x8, y8), f2(q[7], q[8]));
+    const float2 D9_10 = sub2(f2(m9, m10), f2(q[9], q[10]));
+    const float2 D11_12 = sub2(f2(m11, m12), f2(q[11], q[12]));
+    const float2 D5_15 = sub2(f2(m5, m15), f2(q[5], q[15]));
+    const float2 D6_14 = sub2(f2(m6, m14), f2(q[6], q[14]));
+    if (P.has_c9) {
+        // (D8, D9 of the paper's 1-based rows) += (q8, q9) P [u . (4 grad u - (4/b) div u) + 2 u_perp shear]
+        const float Pt = Dev ? C.P0 + dP : dP;
+        const float div = dxux + dyuy, shr = dxuy + dyux;
+        const float2 g = fma2(f2(4.0f, 4.0f), f2(dxux, dyuy), bc2(-C.four_inv_b * div));
+        const float2 h = fma2(f2(ux, uy), g, mul2(bc2(2.0f * shr), f2(uy, ux)));
+        D7_8 = fma2(mul2(ld2(&C.q8), bc2(Pt)), h, D7_8);
+    }
+    const float2 d4 = bc2(D4_13.x), d13 = bc2(D4_13.y);
+    const float2 S01 = fma2(ld2(C.pA[0][1]), d13, mul2(ld2(C.pA[0][0]), d4));
+    const float2 S23 = fma2(ld2(C.pA[1][1]), d13, mul2(ld2(C.pA[1][0]), d4));
+    const float2 d7 = bc2(D7_8.x), d9 = bc2(D9_10.x), d11 = bc2(D11_12.x);
+    const float2 d8 = bc2(D7_8.y), d10 = bc2(D9_10.y), d12 = bc2(D11_12.y);
+    const float2 X01 = fma2(ld2(C.pEx[0][2]), d11, fma2(ld2(C.pEx[0][1]), d9, mul2(ld2(C.pEx[0][0]), d7)));
+    const float2 X23 = fma2(ld2(C.pEx[1][2]), d11, fma2(ld2(C.pEx[1][1]), d9, mul2(ld2(C.pEx[1][0]), d7)));
+    const float2 Y01 = fma2(ld2(C.pEy[0][2]), d12, fma2(ld2(C.pEy[0][1]), d10, mul2(ld2(C.pEy[0][0]), d8)));
+    const float2 Y23 = fma2(ld2(C.pEy[1][2]), d12, fma2(ld2(C.pEy[1][1]), d10, mul2(ld2(C.pEy[1][0]), d8)));
+    const float2 Q01 = fma2(ld2(C.pB1[1]), bc2(D5_15.y), mul2(ld2(C.pB1[0]), bc2(D5_15.x)));
+    const float2 Q23 = fma2(ld2(C.pB2[1]), bc2(D6_14.y), mul2(ld2(C.pB2[0]), bc2(D6_14.x)));
+    unbutterfly2_axis(S01, X01, Y01, Q01, acc);
+    unbutterfly2_diag(S23, X23, Y23, Q23, acc + 4);
 }
 
 }  // namespace lbm

@@ -64,6 +64,25 @@ cudaError_t tma_prepare();   // opt the kernels in to their dynamic shared memor
 // `tmap` points to the CUtensorMap of the input buffer (3-D: pitch x (ny+4) x 16).
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);
 
+// Streaming step kernel: a CTA of WARPS warps owns a strip of W columns and walks down a
+// share of its rows through a ring of SLOTS row slots; a slot holds all planes of one row
+// as two copies of BW columns (half strip + 4 halo columns on each side).
+template <typename R>
+struct StreamShape {
+    static constexpr int WARPS = 8;
+    static constexpr int W = 32 * WARPS;               // strip width
+    static constexpr int BW = W / 2 + 8;               // columns per copy
+    static constexpr int HALF = NQ * BW;               // elements per copy
+    static constexpr int ROW = 2 * HALF;               // elements per slot
+    static constexpr int SLOTS = 6;
+    static constexpr unsigned copy_bytes = HALF * sizeof(R);
+    static constexpr size_t smem_bytes = sizeof(R) * (size_t)SLOTS * ROW;
+};
+bool stream_supported(const Params &P);
+cudaError_t stream_prepare();
+// `tmap` points to the CUtensorMap of the input buffer with box BW x 1 x 16.
+cudaError_t launch_step_stream(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);
+
 // Sustained float64 FMA rate of the current device in FLOP/s (FMA = 2).
 cudaError_t measure_fp64_fma(double *flops);
 

@@ -1,0 +1,498 @@
+// lbm_step_stream.cu -- streaming fused step kernel (sm_103a).
+//
+// Each CTA (8 warps) owns a 256-column strip of the grid and marches down a
+// contiguous range of its rows; the ranges of all CTAs split strips x rows
+// evenly (a range that reaches the bottom of a strip continues at the top of
+// the next one).  Rows of all 16 population planes (the strip plus 4 halo
+// columns on each side) stream through a ring of shared-memory slots.  A slot
+// is filled by two tensor copies (cp.async.bulk.tensor, 136 columns each; the
+// halves overlap by 8 columns so that every warp's stencil lies inside one
+// half) that complete on the slot's mbarrier, and it is refilled with the row
+// SLOTS further on by the warp that releases it last.  The warps advance
+// independently; warp w updates columns 32w .. 32w+31 of the strip, one row
+// per step:
+//   - flow velocity of the next row at its own column (u(y+1), kept in
+//     registers with u(y) and u(y-1)) and of the two columns left and right of
+//     the warp in row y (a 16-lane reduction), for the gradient of u;
+//   - MRT collision with the energy-flux correction (Eq. 3, Sec. II);
+//   - limited x convection from the staged row; limited y convection from a
+//     sliding window per thread that lives for the whole range (each slope
+//     computed once, Sec. III);
+//   - one global write per population.
+// Per-value arithmetic is that of the plain kernel; results agree with it to
+// round-off (summation order of the halo velocities, multiply-add contraction).
+#include <cuda.h>
+
+#include "lbm_internal.h"
+#include "lbm_tma_util.cuh"
+
+namespace lbm {
+
+namespace {
+
+// A CTA's share [b, e) of the sequence strip-major (strip, row), and the row
+// copies it implies: each maximal run of rows y0 .. y1-1 of one strip (a
+// segment) needs the rows y0-2 .. y1+1, in that order.
+struct Span {
+    long long b, e;   // share of the strip-major (strip, row) sequence
+    int K1;           // copies of the first segment
+    int ny;
+
+    __device__ void coords(int k, int &strip, int &row) const
+    {
+        int j, K, y0;
+        if (k < K1) {
+            j = 0;
+            K = 0;
+            y0 = (int)(b % ny);
+        } else {
+            const int jj = (k - K1) / (ny + 4);
+            j = 1 + jj;
+            K = K1 + jj * (ny + 4);
+            y0 = 0;
+        }
+        strip = (int)(b / ny) + j;
+        row = y0 + (k - K) - 2;
+    }
+};
+
+// Ring position of copy index k: slot k % SLOTS and the parity (k / SLOTS) & 1 of the
+// slot's mbarrier phase that the copy completes; advanced one copy at a time.
+template <int SLOTS>
+struct RingPos {
+    int slot;
+    unsigned phase;
+    __device__ __forceinline__ void set(int k)
+    {
+        slot = k % SLOTS;
+        phase = (unsigned)(k / SLOTS) & 1u;
+    }
+    __device__ __forceinline__ void next()
+    {
+        if (++slot == SLOTS) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void issue_row(const CUtensorMap *tm, const Span &sp, int k, unsigned ring_a,
+                                          unsigned bar_a)
+{
+    using S = StreamShape<R>;
+    int strip, row;
+    sp.coords(k, strip, row);
+    const int slot = k % S::SLOTS;
+    const unsigned bar = bar_a + 8u * (unsigned)slot;
+    const unsigned dst = ring_a + (unsigned)slot * (unsigned)(S::ROW * sizeof(R));
+    const int x = strip * S::W;   // padded column of interior column strip * W - 4
+    const int y = row + OY;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2u * S::copy_bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(0), "r"(bar)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst + S::copy_bytes), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x + S::W / 2),
+                 "r"(y), "r"(0), "r"(bar)
+                 : "memory");
+}
+
+// Flow velocity of one cell from 16 lanes (lane q holds population q at p, with
+// velocity (cx, cy)); lanes 0-15 and 16-31 reduce independently.
+template <typename R, bool Dev>
+__device__ __forceinline__ void halo_velocity(const Coef<R> &C, const R *p, R cx, R cy, R &u, R &v)
+{
+    const R g = *p;
+    R a = g, bx = cx * g, by = cy * g;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+    }
+    const R rho = Dev ? C.rho0 + a : a;
+    const R ir = recip(rho);
+    u = bx * ir;
+    v = by * ir;
+}
+
+// Sliding y-window per thread: last value, face difference and oriented slope of
+// each y-moving population (float32: per population pair).
+template <typename R> struct Win;
+template <> struct Win<float> { float2 w[8], d[8], m[8]; };
+template <> struct Win<double> { double w[NQ], d[NQ], m[NQ]; };
+
+// Window at the first row y0 of a segment from rows y0-2 (a), y0-1 (b), y0 (c), y0+1 (d).
+// sy > 0: oriented slope at index c is slope2(D[c-1], D[c]) (D[m] = w[m+1] - w[m]); carry
+//         w(y0), D between y0-1 and y0, slope at y0-1.
+// sy < 0: oriented slope at index c is slope2(-D[c], -D[c-1]); carry w(y0+1), D between y0
+//         and y0+1, slope at y0.
+template <int Lim>
+__device__ __forceinline__ void win_init(Win<float> &W, const float *a, const float *b, const float *c,
+                                         const float *d)
+{
+    constexpr int BW = StreamShape<float>::BW;
+    const float2 m1 = f2(-1.f, -1.f);
+#pragma unroll
+    for (int pr = 0; pr < 8; pr++) {
+        const int qa = pair_q(pr), qb = qa + 4;
+        const int sy = tsgn_y(qa);
+        if (sy == 0) continue;
+        const int oa = qa * BW, ob = qb * BW;
+        if (sy > 0) {
+            const float2 w0 = f2(a[oa], a[ob]), w1 = f2(b[oa], b[ob]), w2 = f2(c[oa], c[ob]);
+            const float2 d0 = sub2(w1, w0), d1 = sub2(w2, w1);
+            W.w[pr] = w2;
+            W.d[pr] = d1;
+            W.m[pr] = slope2x2<Lim>(d0, d1);
+        } else {
+            const float2 w1 = f2(b[oa], b[ob]), w2 = f2(c[oa], c[ob]), w3 = f2(d[oa], d[ob]);
+            const float2 d1 = sub2(w2, w1), d2 = sub2(w3, w2);
+            W.w[pr] = w3;
+            W.d[pr] = d2;
+            W.m[pr] = slope2x2<Lim>(mul2(d2, m1), mul2(d1, m1));
+        }
+    }
+}
+
+template <int Lim>
+__device__ __forceinline__ void win_init(Win<double> &W, const double *a, const double *b, const double *c,
+                                         const double *d)
+{
+    constexpr int BW = StreamShape<double>::BW;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const int sy = tsgn_y(q);
+        if (sy == 0) continue;
+        const int o = q * BW;
+        if (sy > 0) {
+            const double d0 = b[o] - a[o], d1 = c[o] - b[o];
+            W.w[q] = c[o];
+            W.d[q] = d1;
+            W.m[q] = slope2<double, Lim>(d0, d1);
+        } else {
+            const double d1 = c[o] - b[o], d2 = d[o] - c[o];
+            W.w[q] = d[o];
+            W.d[q] = d2;
+            W.m[q] = slope2<double, Lim>(-d2, -d1);
+        }
+    }
+}
+
+// Convection of row y and the write of the new populations.  s0, s1, s2: rows y, y+1, y+2
+// at this thread's column; f: populations of the cell; acc: collision term.
+template <int Lim>
+__device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &W, const float2 *fp, const float2 *acc,
+                                              const float *s0, const float *s1, const float *s2, bool store,
+                                              float *__restrict__ fout, long long plane, long long cg)
+{
+    constexpr int BW = StreamShape<float>::BW;
+    const float2 m1 = f2(-1.f, -1.f);
+#pragma unroll
+    for (int pr = 0; pr < 8; pr++) {
+        const int qa = pair_q(pr), qb = qa + 4;
+        const int sx = tsgn_x(qa), sy = tsgn_y(qa);
+        const int sa = qa >> 2;
+        const int oa = qa * BW, ob = qb * BW;
+        const float2 hh = ld2(&C.hh[sa]);
+        const float2 f0 = fp[pr];
+        float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
+        if (sx != 0)
+            tx = flux_diff2<Lim>(f2(s0[oa - 2 * sx], s0[ob - 2 * sx]), f2(s0[oa - sx], s0[ob - sx]), f0,
+                                 f2(s0[oa + sx], s0[ob + sx]), hh);
+        if (sy != 0) {
+            const float *sn = sy > 0 ? s1 : s2;
+            const float2 wn = f2(sn[oa], sn[ob]);
+            const float2 dn = sub2(wn, W.w[pr]);
+            if (sy > 0) {
+                // flux D(y) + h (slope_y - slope_{y-1})
+                const float2 mn = slope2x2<Lim>(W.d[pr], dn);
+                tyv = Lim == 2 ? W.d[pr] : fma2(hh, sub2(mn, W.m[pr]), W.d[pr]);
+                W.m[pr] = mn;
+            } else {
+                // flux -D(y+1) + h (slope_y - slope_{y+1})
+                const float2 nd = mul2(W.d[pr], m1);
+                const float2 mn = slope2x2<Lim>(mul2(dn, m1), nd);
+                tyv = Lim == 2 ? nd : fma2(hh, sub2(W.m[pr], mn), nd);
+                W.m[pr] = mn;
+            }
+            W.w[pr] = wn;
+            W.d[pr] = dn;
+        }
+        const float2 tot = (sx != 0 && sy != 0) ? add2(tx, tyv) : (sx != 0 ? tx : tyv);
+        const float2 out = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
+        if (store) {
+            fout[qa * plane + cg] = out.x;
+            fout[qb * plane + cg] = out.y;
+        }
+    }
+}
+
+template <int Lim>
+__device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double> &W, const double *f,
+                                              const double *acc, const double *s0, const double *s1,
+                                              const double *s2, bool store, double *__restrict__ fout,
+                                              long long plane, long long cg)
+{
+    constexpr int BW = StreamShape<double>::BW;
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const int sx = tsgn_x(q), sy = tsgn_y(q);
+        const int shell = q >> 2;
+        const int o = q * BW;
+        const double hh = C.hh[shell];
+        double tx = 0.0, tyv = 0.0;
+        if (sx != 0) tx = flux_diff<double, Lim>(s0[o - 2 * sx], s0[o - sx], f[q], s0[o + sx], hh);
+        if (sy != 0) {
+            const double wn = (sy > 0 ? s1 : s2)[o];
+            const double dn = wn - W.w[q];
+            if (sy > 0) {
+                const double mn = slope2<double, Lim>(W.d[q], dn);
+                tyv = Lim == 2 ? W.d[q] : W.d[q] + hh * (mn - W.m[q]);
+                W.m[q] = mn;
+            } else {
+                const double mn = slope2<double, Lim>(-dn, -W.d[q]);
+                tyv = Lim == 2 ? -W.d[q] : -W.d[q] + hh * (W.m[q] - mn);
+                W.m[q] = mn;
+            }
+            W.w[q] = wn;
+            W.d[q] = dn;
+        }
+        const double tot = (sx != 0 && sy != 0) ? tx + tyv : (sx != 0 ? tx : tyv);
+        if (store) fout[q * plane + cg] = (f[q] - acc[q]) - C.cr[shell] * tot;
+    }
+}
+
+}  // namespace
+
+template <typename R, bool Dev, int Lim>
+__global__ void __launch_bounds__(32 * StreamShape<R>::WARPS, sizeof(R) == 4 ? 2 : 1)
+k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, R *__restrict__ fout,
+              int *err)
+{
+    using S = StreamShape<R>;
+    constexpr int BW = S::BW;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    R *ring = reinterpret_cast<R *>(smraw);
+    __shared__ __align__(8) unsigned long long full[S::SLOTS];
+    __shared__ unsigned released[S::SLOTS];
+    __shared__ int abort_flag;
+    __shared__ unsigned long long issued;   // row copies issued so far
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int nx = P.nx, ny = P.ny;
+    const long long T = (long long)((nx + S::W - 1) / S::W) * ny;
+    Span sp;
+    sp.ny = ny;
+    sp.b = T * blockIdx.x / gridDim.x;
+    sp.e = T * (blockIdx.x + 1) / gridDim.x;
+    const long long first_end = sp.b / ny * ny + ny;
+    sp.K1 = (int)((sp.e < first_end ? sp.e : first_end) - sp.b) + 4;
+    const int nseg = sp.e > sp.b ? (int)((sp.e - 1) / ny - sp.b / ny + 1) : 0;
+    const int nload = (int)(sp.e - sp.b) + 4 * nseg;
+    const unsigned ring_a = (unsigned)__cvta_generic_to_shared(ring);
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(full);
+
+    if (tid == 0) {
+        for (int s = 0; s < S::SLOTS; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a + 8u * s) : "memory");
+            released[s] = 0;
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int n0 = nload < S::SLOTS ? nload : S::SLOTS;
+        for (int k = 0; k < n0; k++) issue_row<R>(&tm, sp, k, ring_a, bar_a);
+        issued = (unsigned long long)n0;
+    }
+
+    const Coef<R> &C = coef<R>(P);
+    const int h = w >> 2, wl = w & 3;
+    const int col = 32 * wl + 4 + lane;                          // column inside this warp's half copy
+    const int hcol = lane < 16 ? 32 * wl + 3 : 32 * wl + 36;     // column left / right of the warp
+    const int hq = lane & 15;
+    const R mag = hq < 4 ? R(1.0) : (hq < 8 ? R(6.0) : (hq < 12 ? R(kD3) : R(kD4)));
+    const R cxl = R(tsgn_x(hq)) * mag, cyl = R(tsgn_y(hq)) * mag;
+    const R *half = ring + h * S::HALF;
+    using Pos = RingPos<S::SLOTS>;
+    auto row_at = [&](const Pos &p) { return half + p.slot * S::ROW; };
+    auto wait = [&](const Pos &p) {
+        const bool ok = mbar_wait_or_abort(bar_a + 8u * (unsigned)p.slot, p.phase, &abort_flag);
+        if (!ok && lane == 0) *(volatile int *)&abort_flag = 1;
+        return ok;
+    };
+    // copy k (at ring slot `slot`) is no longer read by this warp; the last of the
+    // CTA's warps to release it refills the slot with copy k + SLOTS
+    auto release = [&](int k, int slot) {
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const unsigned old = atomicAdd(&released[slot], 1u);
+            if ((old + 1) % S::WARPS == 0 && k + S::SLOTS < nload) {
+                __threadfence_block();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_row<R>(&tm, sp, k + S::SLOTS, ring_a, bar_a);
+                atomicMax(&issued, (unsigned long long)(k + S::SLOTS + 1));
+            }
+        }
+    };
+
+    bool ok = true;
+    int kb = 0;   // first copy of the current segment
+    for (long long pos = sp.b; ok && pos < sp.e;) {
+        const int strip = (int)(pos / ny), y0 = (int)(pos % ny);
+        const int len = (int)((long long)(ny - y0) < sp.e - pos ? (long long)(ny - y0) : sp.e - pos);
+        const int gx = strip * S::W + 32 * w + lane;
+        Pos pa, pb, pc, pd;   // copies kb .. kb+3: rows y0-2 .. y0+1
+        pa.set(kb);
+        pb = pa;
+        pb.next();
+        pc = pb;
+        pc.next();
+        pd = pc;
+        pd.next();
+        ok = wait(pa) && wait(pb) && wait(pc) && wait(pd);
+        if (!ok) break;
+        R u_m, v_m, u_0, v_0, ir_0, dummy;
+        flow_at<R, Dev>(C, row_at(pb) + col, BW, u_m, v_m, dummy);
+        flow_at<R, Dev>(C, row_at(pc) + col, BW, u_0, v_0, ir_0);
+        Win<R> W;
+        win_init<Lim>(W, row_at(pa) + col, row_at(pb) + col, row_at(pc) + col, row_at(pd) + col);
+        release(kb, pa.slot);
+        release(kb + 1, pb.slot);
+        Pos p0 = pc, p1 = pd, p2 = pd;   // rows y, y+1, y+2
+        p2.next();
+#pragma unroll 1
+        for (int i = 0; i < len; i++) {
+            if (!(ok = wait(p2))) break;
+            const R *r0 = row_at(p0), *r1 = row_at(p1), *r2 = row_at(p2);
+            R u_p, v_p, ir_p;
+            flow_at<R, Dev>(C, r1 + col, BW, u_p, v_p, ir_p);
+            R uh, vh;
+            halo_velocity<R, Dev>(C, r0 + hq * BW + hcol, cxl, cyl, uh, vh);
+            R uxm = __shfl_up_sync(0xffffffffu, u_0, 1), uxp = __shfl_down_sync(0xffffffffu, u_0, 1);
+            R vxm = __shfl_up_sync(0xffffffffu, v_0, 1), vxp = __shfl_down_sync(0xffffffffu, v_0, 1);
+            if (lane == 0) { uxm = uh; vxm = vh; }
+            if (lane == 31) { uxp = uh; vxp = vh; }
+            const R *s0 = r0 + col;
+            const int y = y0 + i;
+            const long long cg = (long long)(y + OY) * P.pitch + (gx + OX);
+            if constexpr (sizeof(R) == sizeof(float)) {
+                float2 fp[8];
+#pragma unroll
+                for (int pr = 0; pr < 8; pr++) fp[pr] = f2(s0[pair_q(pr) * BW], s0[(pair_q(pr) + 4) * BW]);
+                const Shells2 sh = shells2_of(fp);
+                float drho, jx, jy, de;
+                conserved2_of(sh, drho, jx, jy, de);
+                float2 acc[8];
+                collide2<Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m, acc);
+                convect_store<Lim>(C, W, fp, acc, s0, r1 + col, r2 + col, gx < nx, fout, P.plane, cg);
+            } else {
+                R f[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; q++) f[q] = s0[q * BW];
+                const Shells<R> sh = shells_of(f);
+                R drho, jx, jy, de;
+                conserved_of(sh, drho, jx, jy, de);
+                R acc[NQ];
+                collide<R, Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m, acc);
+                convect_store<Lim>(C, W, f, acc, s0, r1 + col, r2 + col, gx < nx, fout, P.plane, cg);
+            }
+            u_m = u_0;
+            u_0 = u_p;
+            v_m = v_0;
+            v_0 = v_p;
+            ir_0 = ir_p;
+            release(kb + i + 2, p0.slot);
+            p0 = p1;
+            p1 = p2;
+            p2.next();
+        }
+        if (!ok) break;
+        release(kb + len + 2, p0.slot);
+        release(kb + len + 3, p1.slot);
+        kb += len + 4;
+        pos += len;
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    __syncthreads();
+    if (tid == 0 && abort_flag) {
+        // let copies still in flight land before the CTA's shared memory is released (bounded)
+        const int n = (int)issued;
+        for (int k = n > S::SLOTS ? n - S::SLOTS : 0; k < n; k++)
+            mbar_wait(bar_a + 8u * (unsigned)(k % S::SLOTS), (unsigned)(k / S::SLOTS) & 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+bool stream_supported(const Params &P)
+{
+    return P.pitch >= StreamShape<float>::BW && P.pitch % 4 == 0;
+}
+
+template <typename R>
+static int stream_ctas(const Params &P, const void *fn)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * StreamShape<R>::WARPS,
+                                                  StreamShape<R>::smem_bytes);
+    if (sms < 1) sms = 1;
+    if (per_sm < 1) per_sm = 1;
+    const long long T = (long long)((P.nx + StreamShape<R>::W - 1) / StreamShape<R>::W) * P.ny;
+    long long n = (long long)sms * per_sm;
+    const long long by_rows = (T + 31) / 32;   // at least 32 rows per CTA
+    if (by_rows < n) n = by_rows;
+    return n < 1 ? 1 : (int)n;
+}
+
+cudaError_t launch_step_stream(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st)
+{
+    const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
+    if (prec == 0) {
+        using S = StreamShape<double>;
+        double *b = (double *)fout;
+        const void *fn = P.limiter == 0 ? (const void *)k_step_stream<double, false, 0>
+                         : P.limiter == 1 ? (const void *)k_step_stream<double, false, 1>
+                                          : (const void *)k_step_stream<double, false, 2>;
+        const int grid = stream_ctas<double>(P, fn);
+        if (P.limiter == 0) k_step_stream<double, false, 0><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+        else if (P.limiter == 1) k_step_stream<double, false, 1><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+        else k_step_stream<double, false, 2><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+    } else {
+        using S = StreamShape<float>;
+        float *b = (float *)fout;
+        const void *fn = P.limiter == 0 ? (const void *)k_step_stream<float, true, 0>
+                         : P.limiter == 1 ? (const void *)k_step_stream<float, true, 1>
+                                          : (const void *)k_step_stream<float, true, 2>;
+        const int grid = stream_ctas<float>(P, fn);
+        if (P.limiter == 0) k_step_stream<float, true, 0><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+        else if (P.limiter == 1) k_step_stream<float, true, 1><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+        else k_step_stream<float, true, 2><<<grid, 32 * S::WARPS, S::smem_bytes, st>>>(P, tm, b, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t stream_prepare()
+{
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void *)k_step_stream<double, false, 0>, StreamShape<double>::smem_bytes);
+    set((const void *)k_step_stream<double, false, 1>, StreamShape<double>::smem_bytes);
+    set((const void *)k_step_stream<double, false, 2>, StreamShape<double>::smem_bytes);
+    set((const void *)k_step_stream<float, true, 0>, StreamShape<float>::smem_bytes);
+    set((const void *)k_step_stream<float, true, 1>, StreamShape<float>::smem_bytes);
+    set((const void *)k_step_stream<float, true, 2>, StreamShape<float>::smem_bytes);
+    return e;
+}
+
+}  // namespace lbm

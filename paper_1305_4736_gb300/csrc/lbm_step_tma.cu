@@ -16,46 +16,117 @@
 #include <cuda.h>
 
 #include "lbm_internal.h"
+#include "lbm_tma_util.cuh"
 
 namespace lbm {
 
 namespace {
-
-__device__ __forceinline__ constexpr int tsgn_x(int q)
-{
-    return q < 8 ? ((q & 3) == 0 ? 1 : ((q & 3) == 2 ? -1 : 0)) : (((q & 3) == 0 || (q & 3) == 3) ? 1 : -1);
-}
-__device__ __forceinline__ constexpr int tsgn_y(int q)
-{
-    return q < 8 ? ((q & 3) == 1 ? 1 : ((q & 3) == 3 ? -1 : 0)) : (((q & 3) <= 1) ? 1 : -1);
-}
 
 __device__ __forceinline__ bool tu_cell(int x, int y, int nx, int ny)
 {
     return (x >= -1 && x <= nx && y >= 0 && y < ny) || (y >= -1 && y <= ny && x >= 0 && x < nx);
 }
 
-// Bounded wait on phase `phase` of an mbarrier (true when the phase completed).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase)
-{
-    for (int i = 0; i < (1 << 22); i++) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(bar), "r"(phase) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-template <typename R, int Lim>
-__device__ __forceinline__ R slope2(R a, R b)
-{
-    return Lim == 0 ? mc2(a, b) : (Lim == 1 ? R(2.0) * b : R(0.0));
-}
-
 }  // namespace
+
+// Phase 2 of the float32 kernel on population pairs (see flux_diff2).
+template <bool Dev, int Lim>
+__device__ __forceinline__ void phase2_packed(const Params &P, const float *tile, const float *su, const float *sv,
+                                              const float *sir, int lane, int ty, int x0, int y0,
+                                              float *__restrict__ fout)
+{
+    using S = TmaShape<float>;
+    const Coef<float> &C = coef<float>(P);
+    const int gx = x0 + lane;
+    const int r0 = ty * S::KR;
+    const float2 m1 = f2(-1.f, -1.f);
+    // sliding y-window state per y-moving pair: last value, face difference, slope
+    float2 yw[8], yd[8], ym[8];
+#pragma unroll
+    for (int pr = 0; pr < 8; pr++) {
+        const int qa = pair_q(pr), qb = qa + 4;
+        const int sy = tsgn_y(qa);
+        if (sy == 0) continue;
+        const float *pa = tile + qa * S::PL + (lane + 4), *pb = tile + qb * S::PL + (lane + 4);
+        if (sy > 0) {
+            const float2 w0 = f2(pa[r0 * S::SW], pb[r0 * S::SW]);
+            const float2 w1 = f2(pa[(r0 + 1) * S::SW], pb[(r0 + 1) * S::SW]);
+            const float2 w2 = f2(pa[(r0 + 2) * S::SW], pb[(r0 + 2) * S::SW]);
+            const float2 d0 = sub2(w1, w0), d1 = sub2(w2, w1);
+            yw[pr] = w2;
+            yd[pr] = d1;
+            ym[pr] = slope2x2<Lim>(d0, d1);
+        } else {
+            const float2 w1 = f2(pa[(r0 + 1) * S::SW], pb[(r0 + 1) * S::SW]);
+            const float2 w2 = f2(pa[(r0 + 2) * S::SW], pb[(r0 + 2) * S::SW]);
+            const float2 w3 = f2(pa[(r0 + 3) * S::SW], pb[(r0 + 3) * S::SW]);
+            const float2 d1 = sub2(w2, w1), d2 = sub2(w3, w2);
+            yw[pr] = w3;
+            yd[pr] = d2;
+            ym[pr] = slope2x2<Lim>(__fmul2_rn(d2, m1), __fmul2_rn(d1, m1));
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < S::KR; k++) {
+        const int r = r0 + k;
+        const int gy = y0 + r;
+        const float *p = tile + (r + 2) * S::SW + (lane + 4);
+        float2 fp[8];
+#pragma unroll
+        for (int pr = 0; pr < 8; pr++) fp[pr] = f2(p[pair_q(pr) * S::PL], p[(pair_q(pr) + 4) * S::PL]);
+        const Shells2 sh = shells2_of(fp);
+        float drho, jx, jy, de;
+        conserved2_of(sh, drho, jx, jy, de);
+        const int ui = (r + 1) * S::UW + (lane + 1);
+        const float ir = sir[ui];
+        const float dxux = su[ui + 1] - su[ui - 1];
+        const float dyux = su[ui + S::UW] - su[ui - S::UW];
+        const float dxuy = sv[ui + 1] - sv[ui - 1];
+        const float dyuy = sv[ui + S::UW] - sv[ui - S::UW];
+        float2 acc[8];
+        collide2<Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+        const bool store = gx < P.nx && gy < P.ny;
+        const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
+#pragma unroll
+        for (int pr = 0; pr < 8; pr++) {
+            const int qa = pair_q(pr), qb = qa + 4;
+            const int sx = tsgn_x(qa), sy = tsgn_y(qa);
+            const int sa = qa >> 2;
+            const float2 hh = ld2(&C.hh[sa]);
+            const float2 f0 = fp[pr];
+            float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
+            if (sx != 0) {
+                const float *pa = p + qa * S::PL, *pb = p + qb * S::PL;
+                tx = flux_diff2<Lim>(f2(pa[-2 * sx], pb[-2 * sx]), f2(pa[-sx], pb[-sx]), f0,
+                                     f2(pa[sx], pb[sx]), hh);
+            }
+            if (sy != 0) {
+                const float *pa = tile + qa * S::PL + (lane + 4), *pb = tile + qb * S::PL + (lane + 4);
+                const int rn = (r + (sy > 0 ? 3 : 4)) * S::SW;
+                const float2 wn = f2(pa[rn], pb[rn]);
+                const float2 dn = sub2(wn, yw[pr]);
+                if (sy > 0) {
+                    const float2 mn = slope2x2<Lim>(yd[pr], dn);
+                    tyv = Lim == 2 ? yd[pr] : __ffma2_rn(hh, sub2(mn, ym[pr]), yd[pr]);
+                    ym[pr] = mn;
+                } else {
+                    const float2 mn = slope2x2<Lim>(__fmul2_rn(dn, m1), __fmul2_rn(yd[pr], m1));
+                    const float2 nyd = __fmul2_rn(yd[pr], m1);
+                    tyv = Lim == 2 ? nyd : __ffma2_rn(hh, sub2(ym[pr], mn), nyd);
+                    ym[pr] = mn;
+                }
+                yw[pr] = wn;
+                yd[pr] = dn;
+            }
+            const float2 tot = (sx != 0 && sy != 0) ? __fadd2_rn(tx, tyv) : (sx != 0 ? tx : tyv);
+            const float2 out = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
+            if (store) {
+                fout[qa * P.plane + cg] = out.x;
+                fout[qb * P.plane + cg] = out.y;
+            }
+        }
+    }
+}
 
 template <typename R, bool Dev, int Lim>
 __global__ void __launch_bounds__(kTmaTX * kTmaTT, sizeof(R) == 4 ? 2 : 1)
@@ -100,19 +171,8 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     for (int k = tid; k < S::UW * S::UH; k += kTmaTX * kTmaTT) {
         const int i = k % S::UW, j = k / S::UW;
         R ux = R(0), uy = R(0), ir = R(0);
-        if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny)) {
-            const R *p = tile + (j + 1) * S::SW + (i + 3);
-            R g[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; q++) g[q] = p[q * S::PL];
-            const Shells<R> sh = shells_of(g);
-            R drho, jx, jy, de;
-            conserved_of(sh, drho, jx, jy, de);
-            const R rho = Dev ? C.rho0 + drho : drho;
-            ir = recip(rho);
-            ux = jx * ir;
-            uy = jy * ir;
-        }
+        if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny))
+            flow_at<R, Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
         su[k] = ux;
         sv[k] = uy;
         sir[k] = ir;
@@ -120,89 +180,94 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     __syncthreads();
 
     // ---- phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
-    const int gx = x0 + lane;
-    const int r0 = ty * S::KR;
-    // sliding y-window state per y-moving population: last value, face difference, slope
-    R yw[NQ], yd[NQ], ym[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; q++) {
-        const int sy = tsgn_y(q);
-        if (sy == 0) continue;
-        const R *pc = tile + q * S::PL + (lane + 4);
-        // window index m <-> smem row r0 + m (tile row r0 + m - 2); D[m] = w[m+1] - w[m]
-        if (sy > 0) {
-            // oriented slope at index c: slope2(D[c-1], D[c]); carry w[2], D[1], slope at index 1
-            const R w0 = pc[r0 * S::SW], w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW];
-            const R d0 = w1 - w0, d1 = w2 - w1;
-            yw[q] = w2;
-            yd[q] = d1;
-            ym[q] = slope2<R, Lim>(d0, d1);
-        } else {
-            // oriented slope at index c: slope2(-D[c], -D[c-1]); carry w[3], D[2], slope at index 2
-            const R w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
-            const R d1 = w2 - w1, d2 = w3 - w2;
-            yw[q] = w3;
-            yd[q] = d2;
-            ym[q] = slope2<R, Lim>(-d2, -d1);
-        }
-    }
-
-#pragma unroll 1
-    for (int k = 0; k < S::KR; k++) {
-        const int r = r0 + k;
-        const int gy = y0 + r;
-        const R *p = tile + (r + 2) * S::SW + (lane + 4);
-        R f[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; q++) f[q] = p[q * S::PL];
-        const Shells<R> sh = shells_of(f);
-        R drho, jx, jy, de;
-        conserved_of(sh, drho, jx, jy, de);
-        const int ui = (r + 1) * S::UW + (lane + 1);
-        const R ir = sir[ui];
-        const R dxux = su[ui + 1] - su[ui - 1];
-        const R dyux = su[ui + S::UW] - su[ui - S::UW];
-        const R dxuy = sv[ui + 1] - sv[ui - 1];
-        const R dyuy = sv[ui + S::UW] - sv[ui - S::UW];
-        R acc[NQ];
-        collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
-        const bool store = gx < nx && gy < ny;
-        const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        phase2_packed<Dev, Lim>(P, tile, su, sv, sir, lane, ty, x0, y0, fout);
+    } else {
+        const int gx = x0 + lane;
+        const int r0 = ty * S::KR;
+        // sliding y-window state per y-moving population: last value, face difference, slope
+        R yw[NQ], yd[NQ], ym[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
-            const int sx = tsgn_x(q), sy = tsgn_y(q);
-            const int shell = q >> 2;
-            const R hh = C.hh[shell];
-            R tx = R(0), tyv = R(0);
-            if (sx != 0) {
-                // both slopes from the staged row (sharing the upwind slope with the
-                // neighbouring lane would cost a shuffle plus a boundary-lane fix-up)
-                const R *pr = p + q * S::PL;
-                const R fm2 = pr[-2 * sx], fm1 = pr[-sx], fp1 = pr[sx];
-                tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, hh);
+            const int sy = tsgn_y(q);
+            if (sy == 0) continue;
+            const R *pc = tile + q * S::PL + (lane + 4);
+            // window index m <-> smem row r0 + m (tile row r0 + m - 2); D[m] = w[m+1] - w[m]
+            if (sy > 0) {
+                // oriented slope at index c: slope2(D[c-1], D[c]); carry w[2], D[1], slope at index 1
+                const R w0 = pc[r0 * S::SW], w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW];
+                const R d0 = w1 - w0, d1 = w2 - w1;
+                yw[q] = w2;
+                yd[q] = d1;
+                ym[q] = slope2<R, Lim>(d0, d1);
+            } else {
+                // oriented slope at index c: slope2(-D[c], -D[c-1]); carry w[3], D[2], slope at index 2
+                const R w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
+                const R d1 = w2 - w1, d2 = w3 - w2;
+                yw[q] = w3;
+                yd[q] = d2;
+                ym[q] = slope2<R, Lim>(-d2, -d1);
             }
-            if (sy != 0) {
-                const R *pc = tile + q * S::PL + (lane + 4);
-                // next window value: smem row r0 + k + 3 (sy > 0) or r0 + k + 4 (sy < 0)
-                const R wn = pc[(r + (sy > 0 ? 3 : 4)) * S::SW];
-                const R dn = wn - yw[q];
-                if (sy > 0) {
-                    // D[k+2], slope at J = index k+2; flux D[k+1] + h (slope_J - slope_{J-1})
-                    const R mn = slope2<R, Lim>(yd[q], dn);
-                    tyv = Lim == 2 ? yd[q] : yd[q] + hh * (mn - ym[q]);
-                    ym[q] = mn;
-                } else {
-                    // D[k+3], slope at J - sigma = index k+3; flux -D[k+2] + h (slope_J - slope_{J+1})
-                    const R mn = slope2<R, Lim>(-dn, -yd[q]);
-                    tyv = Lim == 2 ? -yd[q] : -yd[q] + hh * (ym[q] - mn);
-                    ym[q] = mn;
-                }
-                yw[q] = wn;
-                yd[q] = dn;
-            }
-            const R tot = (sx != 0 && sy != 0) ? tx + tyv : (sx != 0 ? tx : tyv);
-            if (store) fout[q * P.plane + cg] = (f[q] - acc[q]) - C.cr[shell] * tot;
         }
+
+#pragma unroll 1
+        for (int k = 0; k < S::KR; k++) {
+            const int r = r0 + k;
+            const int gy = y0 + r;
+            const R *p = tile + (r + 2) * S::SW + (lane + 4);
+            R f[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; q++) f[q] = p[q * S::PL];
+            const Shells<R> sh = shells_of(f);
+            R drho, jx, jy, de;
+            conserved_of(sh, drho, jx, jy, de);
+            const int ui = (r + 1) * S::UW + (lane + 1);
+            const R ir = sir[ui];
+            const R dxux = su[ui + 1] - su[ui - 1];
+            const R dyux = su[ui + S::UW] - su[ui - S::UW];
+            const R dxuy = sv[ui + 1] - sv[ui - 1];
+            const R dyuy = sv[ui + S::UW] - sv[ui - S::UW];
+            R acc[NQ];
+            collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+            const bool store = gx < nx && gy < ny;
+            const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                const int sx = tsgn_x(q), sy = tsgn_y(q);
+                const int shell = q >> 2;
+                const R hh = C.hh[shell];
+                R tx = R(0), tyv = R(0);
+                if (sx != 0) {
+                    // both slopes from the staged row (sharing the upwind slope with the
+                    // neighbouring lane would cost a shuffle plus a boundary-lane fix-up)
+                    const R *pr = p + q * S::PL;
+                    const R fm2 = pr[-2 * sx], fm1 = pr[-sx], fp1 = pr[sx];
+                    tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, hh);
+                }
+                if (sy != 0) {
+                    const R *pc = tile + q * S::PL + (lane + 4);
+                    // next window value: smem row r0 + k + 3 (sy > 0) or r0 + k + 4 (sy < 0)
+                    const R wn = pc[(r + (sy > 0 ? 3 : 4)) * S::SW];
+                    const R dn = wn - yw[q];
+                    if (sy > 0) {
+                        // D[k+2], slope at J = index k+2; flux D[k+1] + h (slope_J - slope_{J-1})
+                        const R mn = slope2<R, Lim>(yd[q], dn);
+                        tyv = Lim == 2 ? yd[q] : yd[q] + hh * (mn - ym[q]);
+                        ym[q] = mn;
+                    } else {
+                        // D[k+3], slope at J - sigma = index k+3; flux -D[k+2] + h (slope_J - slope_{J+1})
+                        const R mn = slope2<R, Lim>(-dn, -yd[q]);
+                        tyv = Lim == 2 ? -yd[q] : -yd[q] + hh * (ym[q] - mn);
+                        ym[q] = mn;
+                    }
+                    yw[q] = wn;
+                    yd[q] = dn;
+                }
+                const R tot = (sx != 0 && sy != 0) ? tx + tyv : (sx != 0 ? tx : tyv);
+                if (store) fout[q * P.plane + cg] = (f[q] - acc[q]) - C.cr[shell] * tot;
+            }
+        }
+
     }
 }
 

@@ -1,0 +1,103 @@
+// lbm_tma_util.cuh -- device helpers shared by the shared-memory-staged step
+// kernels: stencil orientation of each population, the bounded mbarrier wait,
+// and the limited flux difference in scalar and packed float32-pair form.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+__device__ __forceinline__ constexpr int tsgn_x(int q)
+{
+    return q < 8 ? ((q & 3) == 0 ? 1 : ((q & 3) == 2 ? -1 : 0)) : (((q & 3) == 0 || (q & 3) == 3) ? 1 : -1);
+}
+__device__ __forceinline__ constexpr int tsgn_y(int q)
+{
+    return q < 8 ? ((q & 3) == 1 ? 1 : ((q & 3) == 3 ? -1 : 0)) : (((q & 3) <= 1) ? 1 : -1);
+}
+
+// Waits on an mbarrier phase.  try_wait carries a suspend-time hint, so a waiting warp
+// sleeps until the phase completes (or the hint runs out) instead of spinning on issue
+// slots that the other warps need; the wait as a whole is bounded by the global timer.
+constexpr unsigned kWaitHintNs = 20000;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned phase)
+{
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(phase), "r"(kWaitHintNs) : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on phase `phase` of an mbarrier (true when the phase completed).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < kWaitLimitNs)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// As mbar_wait, but gives up early once another warp of the CTA has raised `abort`.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned phase, const volatile int *abort)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < kWaitLimitNs) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+template <typename R, int Lim>
+__device__ __forceinline__ R slope2(R a, R b)
+{
+    return Lim == 0 ? mc2(a, b) : (Lim == 1 ? R(2.0) * b : R(0.0));
+}
+
+// ---- packed float32 pairs (Blackwell f32x2 arithmetic) -------------------
+// Populations q and q + 4 (q = 0..3 axis shells 1 and 2, q = 8..11 diagonal shells 3 and 4)
+// move in the same direction: their stencils have the same offsets and only the per-shell
+// constants differ, so their convection runs as one float2 per pair.
+
+template <int Lim>
+__device__ __forceinline__ float2 slope2x2(float2 a, float2 b)
+{
+    if (Lim == 2) return f2(0.f, 0.f);
+    if (Lim == 1) return __fmul2_rn(b, f2(2.f, 2.f));
+    const float2 s = __fadd2_rn(a, b);
+    float tx, ty;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(tx) : "f"(a.x), "f"(b.x));
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(ty) : "f"(a.y), "f"(b.y));
+    const float2 t4 = __fmul2_rn(f2(tx, ty), f2(4.f, 4.f));
+    const float rx = fmaxf(fminf(t4.x, fabsf(s.x)), 0.f), ry = fmaxf(fminf(t4.y, fabsf(s.y)), 0.f);
+    return f2(copysignf(rx, b.x), copysignf(ry, b.y));
+}
+
+// (F_out - F_in) of a pair in upwind order (f_{J-2s}, f_{J-s}, f_J, f_{J+s}); hh = h/2 per member.
+template <int Lim>
+__device__ __forceinline__ float2 flux_diff2(float2 fmm, float2 fm, float2 f0, float2 fp, float2 hh)
+{
+    const float2 d1 = sub2(f0, fm);
+    if (Lim == 2) return d1;
+    const float2 d2 = sub2(fp, f0);
+    const float2 d0 = sub2(fm, fmm);
+    return __ffma2_rn(hh, sub2(slope2x2<Lim>(d1, d2), slope2x2<Lim>(d0, d1)), d1);
+}
+
+
+}  // namespace
+}  // namespace lbm

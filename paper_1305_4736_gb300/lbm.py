@@ -29,7 +29,7 @@ LBM_BC_PERIODIC, LBM_BC_ZERO_GRADIENT, LBM_BC_EQUILIBRIUM, LBM_BC_NEQ_WALL = 0, 
 LBM_FP64, LBM_FP32_DEV = 0, 1
 
 EXPORTS = ["lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_central",
-           "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count",
+           "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count", "lbm_step_kernel",
            "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64", "lbm_totals_noalloc",
            "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy",
            "lbm_last_error", "lbm_destroy"]
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
         lib.lbm_batch_destroy.restype = None
         lib.lbm_step_count.argtypes = [vp]
         lib.lbm_step_count.restype = ctypes.c_longlong
+        lib.lbm_step_kernel.argtypes = [vp]
+        lib.lbm_step_kernel.restype = ctypes.c_int
         lib.lbm_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.lbm_footprint.restype = ctypes.c_size_t
         lib.lbm_last_error.argtypes = [vp]
@@ -267,6 +269,10 @@ def lbm_step_count(h) -> int:
     return int(load().lbm_step_count(h))
 
 
+def lbm_step_kernel(h) -> int:
+    return int(load().lbm_step_kernel(h))
+
+
 def lbm_footprint(nx, ny, precision=LBM_FP64) -> int:
     return int(load().lbm_footprint(int(nx), int(ny), int(precision)))
 
@@ -383,3 +389,8 @@ class Solver:
     @property
     def step_count(self):
         return lbm_step_count(self.h)
+
+    @property
+    def step_kernel(self):
+        """lbm_options.step_kernel code of the fused-step kernel in use (1 .. 5)."""
+        return lbm_step_kernel(self.h)
