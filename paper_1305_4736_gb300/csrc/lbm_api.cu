@@ -239,12 +239,15 @@ bool make_tensor_map(CUtensorMap *tm, void *base, const Params &P, int prec, int
 {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
-    const size_t es = prec == LBM_FP32_DEV ? sizeof(float) : sizeof(double);
-    const cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 4), (cuuint64_t)NQ};
+    // float64: 16 planes of doubles; float32: 8 planes of population pairs, copied as
+    // 8-byte elements (the bits are moved unchanged)
+    const size_t es = 8;
+    const cuuint64_t planes = prec == LBM_FP32_DEV ? NQ / 2 : NQ;
+    const cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 4), planes};
     const cuuint64_t strides[2] = {(cuuint64_t)P.pitch * es, (cuuint64_t)P.plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)NQ};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, (cuuint32_t)planes};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(tm, prec == LBM_FP32_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+    const CUresult r = enc(tm, prec == LBM_FP32_DEV ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                            3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

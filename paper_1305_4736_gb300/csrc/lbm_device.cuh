@@ -108,6 +108,30 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 }
 
 // ---------------------------------------------------------------------------
+// Storage order of the populations.  float64: 16 planes; population q of the
+// cell at offset c of a plane lies at q * plane + c.  float32: 8 planes of
+// population pairs; pair pr holds (pair_q(pr), pair_q(pr) + 4) side by side
+// (one 8-byte element per cell), so that the f32x2 arithmetic reads and writes
+// a pair with one access.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ constexpr int pair_q(int pr) { return pr < 4 ? pr : pr + 4; }   // first member
+__host__ __device__ __forceinline__ constexpr int pair_of(int q) { return (q & 3) | ((q >> 3) << 2); }
+__host__ __device__ __forceinline__ constexpr int member_of(int q) { return (q >> 2) & 1; }
+
+template <typename R>
+__host__ __device__ __forceinline__ long long pidx(int q, long long plane, long long c);
+template <>
+__host__ __device__ __forceinline__ long long pidx<double>(int q, long long plane, long long c)
+{
+    return q * plane + c;
+}
+template <>
+__host__ __device__ __forceinline__ long long pidx<float>(int q, long long plane, long long c)
+{
+    return ((long long)pair_of(q) * plane + c) * 2 + member_of(q);
+}
+
+// ---------------------------------------------------------------------------
 // Shell butterflies
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -389,25 +413,32 @@ __device__ __forceinline__ void conserved2_of(const Shells2 &s, float &rho, floa
 
 __device__ __forceinline__ float2 bc2(float v) { return f2(v, v); }
 
-__host__ __device__ __forceinline__ constexpr int pair_q(int pr) { return pr < 4 ? pr : pr + 4; }   // first member
-
-// Flow velocity and 1/rho of the cell whose population q is at p[q * stride].
-template <typename R, bool Dev>
-__device__ __forceinline__ void flow_at(const Coef<R> &C, const R *p, int stride, R &u, R &v, R &ir)
+// Flow velocity and 1/rho of the cell whose population q is at p[q * stride] (float64
+// planes) or whose pair pr is at p2[pr * stride] (float32 pair planes).
+template <bool Dev>
+__device__ __forceinline__ void flow_at(const Coef<double> &C, const double *p, int stride, double &u, double &v,
+                                        double &ir)
 {
-    R drho, jx, jy, de;
-    if constexpr (sizeof(R) == sizeof(float)) {
-        float2 fp[8];
+    double g[NQ], drho, jx, jy, de;
 #pragma unroll
-        for (int pr = 0; pr < 8; pr++) fp[pr] = f2(p[pair_q(pr) * stride], p[(pair_q(pr) + 4) * stride]);
-        conserved2_of(shells2_of(fp), drho, jx, jy, de);
-    } else {
-        R g[NQ];
+    for (int q = 0; q < NQ; q++) g[q] = p[q * stride];
+    conserved_of(shells_of(g), drho, jx, jy, de);
+    const double rho = Dev ? C.rho0 + drho : drho;
+    ir = recip(rho);
+    u = jx * ir;
+    v = jy * ir;
+}
+
+template <bool Dev>
+__device__ __forceinline__ void flow_at(const Coef<float> &C, const float2 *p2, int stride, float &u, float &v,
+                                        float &ir)
+{
+    float2 fp[8];
 #pragma unroll
-        for (int q = 0; q < NQ; q++) g[q] = p[q * stride];
-        conserved_of(shells_of(g), drho, jx, jy, de);
-    }
-    const R rho = Dev ? C.rho0 + drho : drho;
+    for (int pr = 0; pr < 8; pr++) fp[pr] = p2[pr * stride];
+    float drho, jx, jy, de;
+    conserved2_of(shells2_of(fp), drho, jx, jy, de);
+    const float rho = Dev ? C.rho0 + drho : drho;
     ir = recip(rho);
     u = jx * ir;
     v = jy * ir;

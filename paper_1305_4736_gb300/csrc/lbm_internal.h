@@ -54,7 +54,7 @@ struct TmaShape {
     static constexpr int TR = kTmaTT * KR;             // tile rows
     static constexpr int SW = kTmaTX + 8;              // staged row: x halo of 4 (16-byte TMA origin)
     static constexpr int SH = TR + 4;                  // staged rows: y halo of 2
-    static constexpr int PL = SW * SH;                 // staged plane
+    static constexpr int PL = SW * SH;                 // staged plane (float32: plane of pairs, in pairs)
     static constexpr int UW = kTmaTX + 2, UH = TR + 2; // flow-velocity tile with its ring
     static constexpr size_t tile_bytes = sizeof(R) * NQ * PL;
     static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * 3 * UW * UH;
@@ -66,7 +66,8 @@ cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *f
 
 // Streaming step kernel: a CTA of WARPS warps owns a strip of W columns and walks down a
 // share of its rows through a ring of SLOTS row slots; a slot holds all planes of one row
-// as two copies of BW columns (half strip + 4 halo columns on each side).
+// as two copies of BW columns (half strip + 4 halo columns on each side).  Sizes in
+// elements of R (float32: 8 planes of pairs = 16 floats per column).
 template <typename R>
 struct StreamShape {
     static constexpr int WARPS = 8;

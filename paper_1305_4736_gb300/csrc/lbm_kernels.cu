@@ -10,9 +10,9 @@
 //   k_totals_* deterministic two-pass float64 totals of rho, j, e
 //   k_pack / k_unpack  interior populations to / from a dense float64 buffer
 //
-// Storage: population planes q = 0..15 of (ny + 4) rows by `pitch` columns;
-// interior cell (x, y) at row y + 2, column x + 4.  R = double stores f;
-// R = float stores g = f - f^eq0 (deviation mode).
+// Storage: population planes of (ny + 4) rows by `pitch` columns; interior cell
+// (x, y) at row y + 2, column x + 4.  R = double stores f in 16 planes; R = float
+// stores g = f - f^eq0 (deviation mode) in 8 planes of population pairs (pidx).
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -38,11 +38,21 @@ __device__ __forceinline__ R pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
-template <typename R>
-__device__ __forceinline__ void load16(const R *__restrict__ f, long long plane, long long c, R *out)
+__device__ __forceinline__ void load16(const double *__restrict__ f, long long plane, long long c, double *out)
 {
 #pragma unroll
     for (int q = 0; q < NQ; q++) out[q] = f[q * plane + c];
+}
+
+__device__ __forceinline__ void load16(const float *__restrict__ f, long long plane, long long c, float *out)
+{
+    const float2 *f2p = reinterpret_cast<const float2 *>(f);
+#pragma unroll
+    for (int pr = 0; pr < 8; pr++) {
+        const float2 v = f2p[pr * plane + c];
+        out[pair_q(pr)] = v.x;
+        out[pair_q(pr) + 4] = v.y;
+    }
 }
 
 template <typename R, bool Dev>
@@ -131,19 +141,15 @@ __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__
             const int sx = sgn_x(q), sy = sgn_y(q);
             const int shell = q >> 2;
             const R hh = C.hh[shell];
-            const R *fq = fin + q * plane;
+            auto at = [&](long long c) { return fin[pidx<R>(q, plane, c)]; };
             R tx_ = R(0), ty_ = R(0);
-            if (sx != 0) {
-                const R fmm = fq[c0 - 2 * sx], fm = fq[c0 - sx], fp = fq[c0 + sx];
-                tx_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
-            }
+            if (sx != 0) tx_ = flux_diff<R, Lim>(at(c0 - 2 * sx), at(c0 - sx), f[q], at(c0 + sx), hh);
             if (sy != 0) {
                 const long long sp = (long long)sy * pitch;
-                const R fmm = fq[c0 - 2 * sp], fm = fq[c0 - sp], fp = fq[c0 + sp];
-                ty_ = flux_diff<R, Lim>(fmm, fm, f[q], fp, hh);
+                ty_ = flux_diff<R, Lim>(at(c0 - 2 * sp), at(c0 - sp), f[q], at(c0 + sp), hh);
             }
             const R tot = (sx != 0 && sy != 0) ? tx_ + ty_ : (sx != 0 ? tx_ : ty_);
-            fout[q * plane + c0] = acc[q] - C.cr[shell] * tot;
+            fout[pidx<R>(q, plane, c0)] = acc[q] - C.cr[shell] * tot;
         }
     }
 }
@@ -230,10 +236,10 @@ __device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, i
     if (E.kind == 0 || E.kind == 1) {                       // periodic / zero gradient
         const long long cs = (long long)(sy + OY) * P.pitch + (sx + OX);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) f[q * plane + cg] = f[q * plane + cs];
+        for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = f[pidx<R>(q, plane, cs)];
     } else if (E.kind == 2) {                               // fixed equilibrium
 #pragma unroll
-        for (int q = 0; q < NQ; q++) f[q * plane + cg] = pick<R>(E.feq[q], E.feqf[q]);
+        for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = pick<R>(E.feq[q], E.feqf[q]);
     } else {                                                // non-equilibrium extrapolation wall
         const long long cm = (long long)(my + OY) * P.pitch + (mx + OX);
         R g[NQ];
@@ -258,7 +264,7 @@ __device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, i
         for (int q = 0; q < NQ; q++) d[q] = qg[q] - qm[q];
         pop_from_moments(C, d, fd);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) f[q * plane + cg] = g[q] + fd[q];
+        for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = g[q] + fd[q];
     }
 }
 
@@ -302,7 +308,7 @@ __global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, cons
     pop_from_moments(C, q, g);
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
 #pragma unroll
-    for (int qq = 0; qq < NQ; qq++) f[qq * P.plane + c] = R(g[qq]);
+    for (int qq = 0; qq < NQ; qq++) f[pidx<R>(qq, P.plane, c)] = R(g[qq]);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,7 +356,7 @@ __global__ void k_moments(const __grid_constant__ Params P, const R *__restrict_
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
     double g[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; q++) g[q] = (double)f[q * P.plane + c];
+    for (int q = 0; q < NQ; q++) g[q] = (double)f[pidx<R>(q, P.plane, c)];
     double rho, ux, uy, T, D[NQ], ir;
     moment_rows<Dev>(P, g, rho, ux, uy, T, D, ir);
     if (!(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(T)) atomicOr(flag, 1);
@@ -429,7 +435,7 @@ k_totals_partial(const __grid_constant__ Params P, const R *__restrict__ f, doub
         const int x = (int)(i % P.nx), y = (int)(i / P.nx);
         const long long c = (long long)(y + OY) * P.pitch + (x + OX);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) run[q] += f[q * P.plane + c];
+        for (int q = 0; q < NQ; q++) run[q] += f[pidx<R>(q, P.plane, c)];
         if (sizeof(R) == sizeof(double) || ++cnt == 32) {
 #pragma unroll
             for (int q = 0; q < NQ; q++) { a[q] += (double)run[q]; run[q] = R(0); }
@@ -503,7 +509,7 @@ __global__ void k_pack(const __grid_constant__ Params P, const R *__restrict__ f
     const int x = (int)(i % P.nx), y = row0 + (int)(i / P.nx);
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
 #pragma unroll
-    for (int q = 0; q < NQ; q++) out[q * n + i] = (double)f[q * P.plane + c] + (Dev ? P.feq0[q] : 0.0);
+    for (int q = 0; q < NQ; q++) out[q * n + i] = (double)f[pidx<R>(q, P.plane, c)] + (Dev ? P.feq0[q] : 0.0);
 }
 
 template <typename R, bool Dev>
@@ -516,7 +522,7 @@ __global__ void k_unpack(const __grid_constant__ Params P, R *__restrict__ f, in
     const int x = (int)(i % P.nx), y = row0 + (int)(i / P.nx);
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
 #pragma unroll
-    for (int q = 0; q < NQ; q++) f[q * P.plane + c] = R(in[q * n + i] - (Dev ? P.feq0[q] : 0.0));
+    for (int q = 0; q < NQ; q++) f[pidx<R>(q, P.plane, c)] = R(in[q * n + i] - (Dev ? P.feq0[q] : 0.0));
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,8 @@
 // round-off (summation order of the halo velocities, multiply-add contraction).
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 #include "lbm_tma_util.cuh"
 
@@ -132,27 +134,24 @@ template <> struct Win<double> { double w[NQ], d[NQ], m[NQ]; };
 // sy < 0: oriented slope at index c is slope2(-D[c], -D[c-1]); carry w(y0+1), D between y0
 //         and y0+1, slope at y0.
 template <int Lim>
-__device__ __forceinline__ void win_init(Win<float> &W, const float *a, const float *b, const float *c,
-                                         const float *d)
+__device__ __forceinline__ void win_init(Win<float> &W, const float2 *a, const float2 *b, const float2 *c,
+                                         const float2 *d)
 {
     constexpr int BW = StreamShape<float>::BW;
     const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
     for (int pr = 0; pr < 8; pr++) {
-        const int qa = pair_q(pr), qb = qa + 4;
-        const int sy = tsgn_y(qa);
+        const int sy = tsgn_y(pair_q(pr));
         if (sy == 0) continue;
-        const int oa = qa * BW, ob = qb * BW;
+        const int o = pr * BW;
         if (sy > 0) {
-            const float2 w0 = f2(a[oa], a[ob]), w1 = f2(b[oa], b[ob]), w2 = f2(c[oa], c[ob]);
-            const float2 d0 = sub2(w1, w0), d1 = sub2(w2, w1);
-            W.w[pr] = w2;
+            const float2 d0 = sub2(b[o], a[o]), d1 = sub2(c[o], b[o]);
+            W.w[pr] = c[o];
             W.d[pr] = d1;
             W.m[pr] = slope2x2<Lim>(d0, d1);
         } else {
-            const float2 w1 = f2(b[oa], b[ob]), w2 = f2(c[oa], c[ob]), w3 = f2(d[oa], d[ob]);
-            const float2 d1 = sub2(w2, w1), d2 = sub2(w3, w2);
-            W.w[pr] = w3;
+            const float2 d1 = sub2(c[o], b[o]), d2 = sub2(d[o], c[o]);
+            W.w[pr] = d[o];
             W.d[pr] = d2;
             W.m[pr] = slope2x2<Lim>(mul2(d2, m1), mul2(d1, m1));
         }
@@ -187,26 +186,24 @@ __device__ __forceinline__ void win_init(Win<double> &W, const double *a, const 
 // at this thread's column; f: populations of the cell; acc: collision term.
 template <int Lim>
 __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &W, const float2 *fp, const float2 *acc,
-                                              const float *s0, const float *s1, const float *s2, bool store,
+                                              const float2 *s0, const float2 *s1, const float2 *s2, bool store,
                                               float *__restrict__ fout, long long plane, long long cg)
 {
     constexpr int BW = StreamShape<float>::BW;
     const float2 m1 = f2(-1.f, -1.f);
+    float2 *out2 = reinterpret_cast<float2 *>(fout);
 #pragma unroll
     for (int pr = 0; pr < 8; pr++) {
-        const int qa = pair_q(pr), qb = qa + 4;
+        const int qa = pair_q(pr);
         const int sx = tsgn_x(qa), sy = tsgn_y(qa);
         const int sa = qa >> 2;
-        const int oa = qa * BW, ob = qb * BW;
+        const int o = pr * BW;
         const float2 hh = ld2(&C.hh[sa]);
         const float2 f0 = fp[pr];
         float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
-        if (sx != 0)
-            tx = flux_diff2<Lim>(f2(s0[oa - 2 * sx], s0[ob - 2 * sx]), f2(s0[oa - sx], s0[ob - sx]), f0,
-                                 f2(s0[oa + sx], s0[ob + sx]), hh);
+        if (sx != 0) tx = flux_diff2<Lim>(s0[o - 2 * sx], s0[o - sx], f0, s0[o + sx], hh);
         if (sy != 0) {
-            const float *sn = sy > 0 ? s1 : s2;
-            const float2 wn = f2(sn[oa], sn[ob]);
+            const float2 wn = (sy > 0 ? s1 : s2)[o];
             const float2 dn = sub2(wn, W.w[pr]);
             if (sy > 0) {
                 // flux D(y) + h (slope_y - slope_{y-1})
@@ -224,11 +221,7 @@ __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &
             W.d[pr] = dn;
         }
         const float2 tot = (sx != 0 && sy != 0) ? add2(tx, tyv) : (sx != 0 ? tx : tyv);
-        const float2 out = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
-        if (store) {
-            fout[qa * plane + cg] = out.x;
-            fout[qb * plane + cg] = out.y;
-        }
+        if (store) out2[pr * plane + cg] = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
     }
 }
 
@@ -322,6 +315,10 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
     const R *half = ring + h * S::HALF;
     using Pos = RingPos<S::SLOTS>;
     auto row_at = [&](const Pos &p) { return half + p.slot * S::ROW; };
+    // a slot row seen from this lane's column: float64 planes of R, float32 planes of pairs
+    using V = std::conditional_t<sizeof(R) == sizeof(float), float2, double>;
+    auto colp = [&](const R *row) { return reinterpret_cast<const V *>(row) + col; };
+    const int hoff = sizeof(R) == sizeof(float) ? (pair_of(hq) * BW + hcol) * 2 + member_of(hq) : hq * BW + hcol;
     auto wait = [&](const Pos &p) {
         const bool ok = mbar_wait_or_abort(bar_a + 8u * (unsigned)p.slot, p.phase, &abort_flag);
         if (!ok && lane == 0) *(volatile int *)&abort_flag = 1;
@@ -360,10 +357,10 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
         ok = wait(pa) && wait(pb) && wait(pc) && wait(pd);
         if (!ok) break;
         R u_m, v_m, u_0, v_0, ir_0, dummy;
-        flow_at<R, Dev>(C, row_at(pb) + col, BW, u_m, v_m, dummy);
-        flow_at<R, Dev>(C, row_at(pc) + col, BW, u_0, v_0, ir_0);
+        flow_at<Dev>(C, colp(row_at(pb)), BW, u_m, v_m, dummy);
+        flow_at<Dev>(C, colp(row_at(pc)), BW, u_0, v_0, ir_0);
         Win<R> W;
-        win_init<Lim>(W, row_at(pa) + col, row_at(pb) + col, row_at(pc) + col, row_at(pd) + col);
+        win_init<Lim>(W, colp(row_at(pa)), colp(row_at(pb)), colp(row_at(pc)), colp(row_at(pd)));
         release(kb, pa.slot);
         release(kb + 1, pb.slot);
         Pos p0 = pc, p1 = pd, p2 = pd;   // rows y, y+1, y+2
@@ -373,36 +370,38 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
             if (!(ok = wait(p2))) break;
             const R *r0 = row_at(p0), *r1 = row_at(p1), *r2 = row_at(p2);
             R u_p, v_p, ir_p;
-            flow_at<R, Dev>(C, r1 + col, BW, u_p, v_p, ir_p);
+            flow_at<Dev>(C, colp(r1), BW, u_p, v_p, ir_p);
             R uh, vh;
-            halo_velocity<R, Dev>(C, r0 + hq * BW + hcol, cxl, cyl, uh, vh);
+            halo_velocity<R, Dev>(C, r0 + hoff, cxl, cyl, uh, vh);
             R uxm = __shfl_up_sync(0xffffffffu, u_0, 1), uxp = __shfl_down_sync(0xffffffffu, u_0, 1);
             R vxm = __shfl_up_sync(0xffffffffu, v_0, 1), vxp = __shfl_down_sync(0xffffffffu, v_0, 1);
             if (lane == 0) { uxm = uh; vxm = vh; }
             if (lane == 31) { uxp = uh; vxp = vh; }
-            const R *s0 = r0 + col;
             const int y = y0 + i;
             const long long cg = (long long)(y + OY) * P.pitch + (gx + OX);
             if constexpr (sizeof(R) == sizeof(float)) {
+                const float2 *s0 = colp(r0);
                 float2 fp[8];
 #pragma unroll
-                for (int pr = 0; pr < 8; pr++) fp[pr] = f2(s0[pair_q(pr) * BW], s0[(pair_q(pr) + 4) * BW]);
+                for (int pr = 0; pr < 8; pr++) fp[pr] = s0[pr * BW];
                 const Shells2 sh = shells2_of(fp);
                 float drho, jx, jy, de;
                 conserved2_of(sh, drho, jx, jy, de);
                 float2 acc[8];
                 collide2<Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m, acc);
-                convect_store<Lim>(C, W, fp, acc, s0, r1 + col, r2 + col, gx < nx, fout, P.plane, cg);
+                convect_store<Lim>(C, W, fp, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg);
             } else {
-                R f[NQ];
+                const double *s0 = colp(r0);
+                double f[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; q++) f[q] = s0[q * BW];
-                const Shells<R> sh = shells_of(f);
-                R drho, jx, jy, de;
+                const Shells<double> sh = shells_of(f);
+                double drho, jx, jy, de;
                 conserved_of(sh, drho, jx, jy, de);
-                R acc[NQ];
-                collide<R, Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m, acc);
-                convect_store<Lim>(C, W, f, acc, s0, r1 + col, r2 + col, gx < nx, fout, P.plane, cg);
+                double acc[NQ];
+                collide<double, Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m,
+                                     acc);
+                convect_store<Lim>(C, W, f, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg);
             }
             u_m = u_0;
             u_0 = u_p;

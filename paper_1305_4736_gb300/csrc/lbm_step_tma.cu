@@ -29,9 +29,10 @@ __device__ __forceinline__ bool tu_cell(int x, int y, int nx, int ny)
 
 }  // namespace
 
-// Phase 2 of the float32 kernel on population pairs (see flux_diff2).
+// Phase 2 of the float32 kernel on population pairs: the staged tile is 8 planes of
+// pairs (pair_q(pr), pair_q(pr) + 4), read and written one pair per access.
 template <bool Dev, int Lim>
-__device__ __forceinline__ void phase2_packed(const Params &P, const float *tile, const float *su, const float *sv,
+__device__ __forceinline__ void phase2_packed(const Params &P, const float2 *tile, const float *su, const float *sv,
                                               const float *sir, int lane, int ty, int x0, int y0,
                                               float *__restrict__ fout)
 {
@@ -40,40 +41,37 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float *tile
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
     const float2 m1 = f2(-1.f, -1.f);
+    const float2 *col = tile + (lane + 4);
     // sliding y-window state per y-moving pair: last value, face difference, slope
     float2 yw[8], yd[8], ym[8];
 #pragma unroll
     for (int pr = 0; pr < 8; pr++) {
-        const int qa = pair_q(pr), qb = qa + 4;
-        const int sy = tsgn_y(qa);
+        const int sy = tsgn_y(pair_q(pr));
         if (sy == 0) continue;
-        const float *pa = tile + qa * S::PL + (lane + 4), *pb = tile + qb * S::PL + (lane + 4);
+        const float2 *pc = col + pr * S::PL;
         if (sy > 0) {
-            const float2 w0 = f2(pa[r0 * S::SW], pb[r0 * S::SW]);
-            const float2 w1 = f2(pa[(r0 + 1) * S::SW], pb[(r0 + 1) * S::SW]);
-            const float2 w2 = f2(pa[(r0 + 2) * S::SW], pb[(r0 + 2) * S::SW]);
+            const float2 w0 = pc[r0 * S::SW], w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW];
             const float2 d0 = sub2(w1, w0), d1 = sub2(w2, w1);
             yw[pr] = w2;
             yd[pr] = d1;
             ym[pr] = slope2x2<Lim>(d0, d1);
         } else {
-            const float2 w1 = f2(pa[(r0 + 1) * S::SW], pb[(r0 + 1) * S::SW]);
-            const float2 w2 = f2(pa[(r0 + 2) * S::SW], pb[(r0 + 2) * S::SW]);
-            const float2 w3 = f2(pa[(r0 + 3) * S::SW], pb[(r0 + 3) * S::SW]);
+            const float2 w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
             const float2 d1 = sub2(w2, w1), d2 = sub2(w3, w2);
             yw[pr] = w3;
             yd[pr] = d2;
-            ym[pr] = slope2x2<Lim>(__fmul2_rn(d2, m1), __fmul2_rn(d1, m1));
+            ym[pr] = slope2x2<Lim>(mul2(d2, m1), mul2(d1, m1));
         }
     }
+    float2 *out2 = reinterpret_cast<float2 *>(fout);
 #pragma unroll 1
     for (int k = 0; k < S::KR; k++) {
         const int r = r0 + k;
         const int gy = y0 + r;
-        const float *p = tile + (r + 2) * S::SW + (lane + 4);
+        const float2 *p = col + (r + 2) * S::SW;
         float2 fp[8];
 #pragma unroll
-        for (int pr = 0; pr < 8; pr++) fp[pr] = f2(p[pair_q(pr) * S::PL], p[(pair_q(pr) + 4) * S::PL]);
+        for (int pr = 0; pr < 8; pr++) fp[pr] = p[pr * S::PL];
         const Shells2 sh = shells2_of(fp);
         float drho, jx, jy, de;
         conserved2_of(sh, drho, jx, jy, de);
@@ -89,41 +87,32 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float *tile
         const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
 #pragma unroll
         for (int pr = 0; pr < 8; pr++) {
-            const int qa = pair_q(pr), qb = qa + 4;
+            const int qa = pair_q(pr);
             const int sx = tsgn_x(qa), sy = tsgn_y(qa);
             const int sa = qa >> 2;
             const float2 hh = ld2(&C.hh[sa]);
             const float2 f0 = fp[pr];
+            const float2 *pp = p + pr * S::PL;
             float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
-            if (sx != 0) {
-                const float *pa = p + qa * S::PL, *pb = p + qb * S::PL;
-                tx = flux_diff2<Lim>(f2(pa[-2 * sx], pb[-2 * sx]), f2(pa[-sx], pb[-sx]), f0,
-                                     f2(pa[sx], pb[sx]), hh);
-            }
+            if (sx != 0) tx = flux_diff2<Lim>(pp[-2 * sx], pp[-sx], f0, pp[sx], hh);
             if (sy != 0) {
-                const float *pa = tile + qa * S::PL + (lane + 4), *pb = tile + qb * S::PL + (lane + 4);
-                const int rn = (r + (sy > 0 ? 3 : 4)) * S::SW;
-                const float2 wn = f2(pa[rn], pb[rn]);
+                const float2 wn = col[pr * S::PL + (r + (sy > 0 ? 3 : 4)) * S::SW];
                 const float2 dn = sub2(wn, yw[pr]);
                 if (sy > 0) {
                     const float2 mn = slope2x2<Lim>(yd[pr], dn);
-                    tyv = Lim == 2 ? yd[pr] : __ffma2_rn(hh, sub2(mn, ym[pr]), yd[pr]);
+                    tyv = Lim == 2 ? yd[pr] : fma2(hh, sub2(mn, ym[pr]), yd[pr]);
                     ym[pr] = mn;
                 } else {
-                    const float2 mn = slope2x2<Lim>(__fmul2_rn(dn, m1), __fmul2_rn(yd[pr], m1));
-                    const float2 nyd = __fmul2_rn(yd[pr], m1);
-                    tyv = Lim == 2 ? nyd : __ffma2_rn(hh, sub2(ym[pr], mn), nyd);
+                    const float2 nyd = mul2(yd[pr], m1);
+                    const float2 mn = slope2x2<Lim>(mul2(dn, m1), nyd);
+                    tyv = Lim == 2 ? nyd : fma2(hh, sub2(ym[pr], mn), nyd);
                     ym[pr] = mn;
                 }
                 yw[pr] = wn;
                 yd[pr] = dn;
             }
-            const float2 tot = (sx != 0 && sy != 0) ? __fadd2_rn(tx, tyv) : (sx != 0 ? tx : tyv);
-            const float2 out = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
-            if (store) {
-                fout[qa * P.plane + cg] = out.x;
-                fout[qb * P.plane + cg] = out.y;
-            }
+            const float2 tot = (sx != 0 && sy != 0) ? add2(tx, tyv) : (sx != 0 ? tx : tyv);
+            if (store) out2[pr * P.plane + cg] = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
         }
     }
 }
@@ -171,8 +160,12 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     for (int k = tid; k < S::UW * S::UH; k += kTmaTX * kTmaTT) {
         const int i = k % S::UW, j = k / S::UW;
         R ux = R(0), uy = R(0), ir = R(0);
-        if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny))
-            flow_at<R, Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+        if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny)) {
+            if constexpr (sizeof(R) == sizeof(float))
+                flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+            else
+                flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+        }
         su[k] = ux;
         sv[k] = uy;
         sir[k] = ir;
@@ -181,7 +174,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
 
     // ---- phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
     if constexpr (sizeof(R) == sizeof(float)) {
-        phase2_packed<Dev, Lim>(P, tile, su, sv, sir, lane, ty, x0, y0, fout);
+        phase2_packed<Dev, Lim>(P, reinterpret_cast<const float2 *>(tile), su, sv, sir, lane, ty, x0, y0, fout);
     } else {
         const int gx = x0 + lane;
         const int r0 = ty * S::KR;
