@@ -93,13 +93,16 @@ typedef struct {
     void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
-    int step_kernel;               /* fused-step kernel: 0 = automatic (TMA-staged when the grid
-                                      allows, else plain 32 x 8), 1 = plain 32 x 8 tiles
+    int step_kernel;               /* fused-step kernel: 0 = automatic (float64: streaming, float32:
+                                      TMA-staged, where the grid allows; else the other, else
+                                      plain 32 x 8), 1 = plain 32 x 8 tiles
                                       (global-memory stencil), 2 = TMA-staged 32 x 32 tiles (grids of
                                       at least 32 x 32), 3 = plain 32 x 4, 4 = plain 32 x 16,
                                       5 = streaming (CTAs walk 256-column strips row by row
                                       through a ring of TMA-filled row slots; grids of at least
-                                      128 columns); all agree to round-off (see lbm_autotune) */
+                                      128 columns), 6 = persistent TMA-staged 32 x 16 tiles with
+                                      two tile buffers per CTA (LBM_FP32_DEV only); all agree to
+                                      round-off (see lbm_autotune) */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
@@ -168,8 +171,9 @@ int lbm_profile_end(lbm_ctx *ctx, double out[4]);
 int lbm_peak_fp64(int device, double *flops);
 
 /* Pick the fastest fused-step kernel for this context's grid: times `reps` launches of
-   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles and the
-   streaming kernel when the grid allows) on the context's current state, writing the spare buffer without advancing the
+   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles, the
+   streaming kernel and the double-buffered TMA-staged kernel when the grid and precision
+   allow) on the context's current state, writing the spare buffer without advancing the
    state, and keeps the fastest for later lbm_step calls.  *choice (may be NULL) receives
    the lbm_options.step_kernel code of the winner.  Synchronous.  Not part of the paper's
    method: a throughput tool. */
@@ -220,7 +224,7 @@ int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream,
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* The lbm_options.step_kernel code (1 .. 5) of the fused-step kernel this context runs
+/* The lbm_options.step_kernel code (1 .. 6) of the fused-step kernel this context runs
    (after automatic selection or lbm_autotune); -1 for a NULL context. */
 int lbm_step_kernel(const lbm_ctx *ctx);
 

@@ -44,9 +44,11 @@ struct lbm_ctx {
     double *tot_out = nullptr;
     bool use_tma = false;
     bool use_stream = false;
+    bool use_pipe = false;
     int plain_ty = lbm::kTY;      // tile height of the plain step kernel
     CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
     CUtensorMap smap[2];          // row-copy descriptors (streaming kernel)
+    CUtensorMap pmap[2];          // tile-copy descriptors of the double-buffered kernel
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0;
@@ -268,6 +270,14 @@ bool make_row_maps(lbm_ctx *c)
            make_tensor_map(&c->smap[1], c->f[1], c->P, c->prec, S::BW, 1);
 }
 
+bool pipe_ready(lbm_ctx *c)
+{
+    using S = lbm::TmaPipeShape;
+    return c->prec == LBM_FP32_DEV && lbm::tma_pipe_supported(c->P) && lbm::tma_pipe_prepare() == cudaSuccess &&
+           make_tensor_map(&c->pmap[0], c->f[0], c->P, c->prec, S::SW, S::SH) &&
+           make_tensor_map(&c->pmap[1], c->f[1], c->P, c->prec, S::SW, S::SH);
+}
+
 bool stream_ready(lbm_ctx *c)
 {
     return lbm::stream_supported(c->P) && lbm::stream_prepare() == cudaSuccess && make_row_maps(c);
@@ -280,6 +290,8 @@ bool tma_ready(lbm_ctx *c)
 
 cudaError_t launch_fused_step(lbm_ctx *c)
 {
+    if (c->use_pipe)
+        return lbm::launch_step_tma_pipe(c->P, &c->pmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
     if (c->use_stream)
         return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
     if (c->use_tma)
@@ -447,15 +459,19 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
     const int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 5) {
+    if (want < 0 || want > 6) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
     if (want == 3) c->plain_ty = 4;
     if (want == 4) c->plain_ty = 16;
-    if (want == 5 && stream_ready(c)) c->use_stream = true;
+    // automatic: float64 runs the streaming kernel (fewer float64 operations per cell), float32
+    // the TMA-staged tile kernel (fewer instructions per cell); each falls back to the other
+    // and then to the plain kernel where the grid or driver does not allow it
+    if ((want == 5 || (want == 0 && prec == LBM_FP64)) && stream_ready(c)) c->use_stream = true;
     if ((want == 2 || (want == 0 && !c->use_stream)) && tma_ready(c)) c->use_tma = true;
-    if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream)) {
+    if (want == 6 && pipe_ready(c)) c->use_pipe = true;
+    if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream) || (want == 6 && !c->use_pipe)) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "requested step kernel unavailable for this grid or driver");
     }
@@ -754,8 +770,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "autotune before lbm_init / lbm_set_state");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
-    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32, 5 = streaming
-    int cands[5] = {1, 3, 4, 0, 0};
+    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32, 5 = streaming,
+    // 6 = double-buffered TMA-staged 32x16 (float32)
+    int cands[6] = {1, 3, 4, 0, 0, 0};
     int ncand = 3;
     const bool tma_ok = c->use_tma || tma_ready(c);
     cudaGetLastError();
@@ -763,6 +780,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     cudaGetLastError();
     if (tma_ok) cands[ncand++] = 2;
     if (stream_ok) cands[ncand++] = 5;
+    const bool pipe_ok = c->use_pipe || pipe_ready(c);
+    cudaGetLastError();
+    if (pipe_ok) cands[ncand++] = 6;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
@@ -773,6 +793,8 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     for (int k = 0; k < ncand && ce == cudaSuccess; k++) {
         auto run = [&]() {
             const int cd = cands[k];
+            if (cd == 6)
+                return lbm::launch_step_tma_pipe(c->P, &c->pmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
             if (cd == 5)
                 return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err,
                                                c->stream);
@@ -796,6 +818,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     if (ce != cudaSuccess) return cuda_fail(c, ce, "autotune");
     c->use_tma = best_c == 2;
     c->use_stream = best_c == 5;
+    c->use_pipe = best_c == 6;
     c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : 8);
     if (choice) *choice = best_c;
     return LBM_OK;
@@ -806,6 +829,7 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 int lbm_step_kernel(const lbm_ctx *c)
 {
     if (!c) return -1;
+    if (c->use_pipe) return 6;
     if (c->use_stream) return 5;
     if (c->use_tma) return 2;
     return c->plain_ty == 4 ? 3 : (c->plain_ty == 16 ? 4 : 1);

@@ -307,10 +307,13 @@ __device__ __forceinline__ float mc2(float a, float b)
 {
     // t = min(|a|, |b|) with sign(a) xor sign(b): negative exactly when the
     // one-sided differences disagree in sign, which the max with 0 turns into 0.
-    float t;
+    // When they agree, a + b has their sign and min.xorsign.abs(max(4t, 0), a + b)
+    // is sign(a + b) min(4 min(|a|, |b|), |a + b|); when they disagree it is +-0.
+    float t, r;
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
-    const float r = fmaxf(fminf(4.0f * t, fabsf(a + b)), 0.0f);
-    return copysignf(r, b);
+    const float m = fmaxf(4.0f * t, 0.0f);
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(m), "f"(a + b));
+    return r;
 }
 
 // 1/x: correctly rounded in float64; in float32 the hardware reciprocal
@@ -486,20 +489,32 @@ __device__ __forceinline__ void collide2(const Params &P, const Shells2 &sh, flo
     const float m5 = fmaf(36.0f, Q1, Q0), m15 = fmaf(1296.0f, Q1, float(kW1) * Q0);
     const float m6 = fmaf(4.5f, Q3, 2.0f * Q2), m14 = fmaf(40.5f, Q3, 8.0f * Q2);
 
-    const float ux = jx * ir, uy = jy * ir;
-    const float J2 = fmaf(jx, ux, jy * uy);
+    // rows 5..16 of f_hat^eq (deviation form, as feq_hat_dev) with the x/y rows in pairs
+    const float2 u2 = mul2(f2(jx, jy), bc2(ir));                  // (u_x, u_y)
+    const float ux = u2.x, uy = u2.y;
+    const float2 jj = mul2(f2(jx, jy), u2);                        // (j_x u_x, j_y u_y)
+    const float J2 = jj.x + jj.y, dxy = jj.x - jj.y;
     const float dP = (de - J2) * C.inv_b;
-    float q[NQ];
-    feq_hat_dev<float, Dev>(C, drho, jx, jy, dP, ir, q);
-    const float2 D4_13 = sub2(f2(m4, m13), f2(q[4], q[13]));
-    float2 D7_8 = sub2(f2(x8, y8), f2(q[7], q[8]));
-    const float2 D9_10 = sub2(f2(m9, m10), f2(q[9], q[10]));
-    const float2 D11_12 = sub2(f2(m11, m12), f2(q[11], q[12]));
-    const float2 D5_15 = sub2(f2(m5, m15), f2(q[5], q[15]));
-    const float2 D6_14 = sub2(f2(m6, m14), f2(q[6], q[14]));
+    const float Pt = Dev ? C.P0 + dP : dP;
+    const float e_dev = fmaf(C.b, dP, J2);
+    const float et = Dev ? C.e0 + e_dev : e_dev;
+    const float q4 = fmaf(2.0f, dP, J2), q5 = dxy, q6 = jx * uy;
+    const float2 q7_8 = mul2(bc2(fmaf(2.0f, Pt, et)), u2);
+    const float2 q9_10 = mul2(bc2(fmaf(4.0f, Pt, J2)), u2);
+    const float2 q11_12 = mul2(add2(bc2(dxy), f2(2.0f * Pt, -2.0f * Pt)), u2);
+    const float T = Pt * ir;
+    const float iso = Dev ? ir * (dP * (Pt + C.P0) - C.P0T0 * drho) : Pt * T;
+    const float q13 = C.two_b2 * iso + C.six_b * T * J2 + J2 * J2 * ir;
+    const float kk = fmaf(C.b4, Pt, J2);
+    const float q14 = kk * ux * uy, q15 = kk * dxy * ir;
+    const float2 D4_13 = sub2(f2(m4, m13), f2(q4, q13));
+    float2 D7_8 = sub2(f2(x8, y8), q7_8);
+    const float2 D9_10 = sub2(f2(m9, m10), q9_10);
+    const float2 D11_12 = sub2(f2(m11, m12), q11_12);
+    const float2 D5_15 = sub2(f2(m5, m15), f2(q5, q15));
+    const float2 D6_14 = sub2(f2(m6, m14), f2(q6, q14));
     if (P.has_c9) {
         // (D8, D9 of the paper's 1-based rows) += (q8, q9) P [u . (4 grad u - (4/b) div u) + 2 u_perp shear]
-        const float Pt = Dev ? C.P0 + dP : dP;
         const float div = dxux + dyuy, shr = dxuy + dyux;
         const float2 g = fma2(f2(4.0f, 4.0f), f2(dxux, dyuy), bc2(-C.four_inv_b * div));
         const float2 h = fma2(f2(ux, uy), g, mul2(bc2(2.0f * shr), f2(uy, ux)));

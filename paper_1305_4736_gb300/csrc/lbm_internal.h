@@ -64,6 +64,24 @@ cudaError_t tma_prepare();   // opt the kernels in to their dynamic shared memor
 // `tmap` points to the CUtensorMap of the input buffer (3-D: pitch x (ny+4) x 16).
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);
 
+// Persistent double-buffered TMA-staged kernel (float32): CTAs walk tiles of kTmaTX columns
+// by TR rows round-robin with two tile buffers, so that the copy of the next tile overlaps
+// the work on the current one; each thread owns KR rows of one column.
+struct TmaPipeShape {
+    static constexpr int KR = 2;
+    static constexpr int TR = kTmaTT * KR;
+    static constexpr int SW = kTmaTX + 8;
+    static constexpr int SH = TR + 4;
+    static constexpr int PL = SW * SH;                 // staged plane of pairs, in pairs
+    static constexpr int UW = kTmaTX + 2, UH = TR + 2;
+    static constexpr size_t buf_bytes = sizeof(float) * NQ * PL;
+    static constexpr size_t smem_bytes = 2 * buf_bytes + sizeof(float) * 3 * UW * UH;
+};
+bool tma_pipe_supported(const Params &P);
+cudaError_t tma_pipe_prepare();
+// `tmap`: CUtensorMap of the input buffer with box SW x SH x 8 pair planes.
+cudaError_t launch_step_tma_pipe(const Params &P, const void *tmap, void *fout, int *err, cudaStream_t st);
+
 // Streaming step kernel: a CTA of WARPS warps owns a strip of W columns and walks down a
 // share of its rows through a ring of SLOTS row slots; a slot holds all planes of one row
 // as two copies of BW columns (half strip + 4 halo columns on each side).  Sizes in

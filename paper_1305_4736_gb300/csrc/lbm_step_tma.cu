@@ -31,12 +31,11 @@ __device__ __forceinline__ bool tu_cell(int x, int y, int nx, int ny)
 
 // Phase 2 of the float32 kernel on population pairs: the staged tile is 8 planes of
 // pairs (pair_q(pr), pair_q(pr) + 4), read and written one pair per access.
-template <bool Dev, int Lim>
+template <bool Dev, int Lim, typename S = TmaShape<float>>
 __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *tile, const float *su, const float *sv,
                                               const float *sir, int lane, int ty, int x0, int y0,
                                               float *__restrict__ fout)
 {
-    using S = TmaShape<float>;
     const Coef<float> &C = coef<float>(P);
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
@@ -262,6 +261,127 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         }
 
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent double-buffered form (float32).  CTA c takes tiles c, c + G, c + 2G, ...
+// (G = grid size); tile k of a CTA is staged in buffer k & 1, whose copy was issued
+// while the CTA worked on tile k - 1 (or at start), and the buffer is refilled with
+// tile k + 2 as soon as every thread is done with tile k.
+// ---------------------------------------------------------------------------
+template <bool Dev, int Lim>
+__global__ void __launch_bounds__(kTmaTX * kTmaTT, 2)
+k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, float *__restrict__ fout,
+                int *err)
+{
+    using S = TmaPipeShape;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2 *buf = reinterpret_cast<float2 *>(smraw);
+    float *su = reinterpret_cast<float *>(smraw + 2 * S::buf_bytes);
+    float *sv = su + S::UW * S::UH;
+    float *sir = sv + S::UW * S::UH;
+    __shared__ __align__(8) unsigned long long bar[2];
+
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
+    const int nx = P.nx, ny = P.ny;
+    const int ntx = (nx + kTmaTX - 1) / kTmaTX;
+    const int ntiles = ntx * ((ny + S::TR - 1) / S::TR);
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(bar);
+    const unsigned buf_a = (unsigned)__cvta_generic_to_shared(buf);
+    // copy of tile t (box origin: interior (x0 - 4, y0 - 2) = padded (x0, y0)) into buffer b
+    auto issue = [&](int t, int b) {
+        const int x0 = (t % ntx) * kTmaTX, y0 = (t / ntx) * S::TR;
+        const unsigned bb = bar_a + 8u * (unsigned)b;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb),
+                     "r"((unsigned)S::buf_bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(buf_a + (unsigned)(b * S::buf_bytes)), "l"(reinterpret_cast<unsigned long long>(&tm)),
+                     "r"(x0), "r"(y0), "r"(0), "r"(bb) : "memory");
+    };
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+    }
+
+    const Coef<float> &C = P.cf;
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, k++) {
+        const int b = k & 1;
+        const bool ok = mbar_wait(bar_a + 8u * (unsigned)b, (unsigned)(k >> 1) & 1u);
+        const float2 *tile = buf + b * (int)(S::buf_bytes / sizeof(float2));
+        const int x0 = (t % ntx) * kTmaTX, y0 = (t / ntx) * S::TR;
+        // phase 1: flow velocity and 1/rho on the tile plus its ring
+        if (ok)
+            for (int kk = tid; kk < S::UW * S::UH; kk += kTmaTX * kTmaTT) {
+                const int i = kk % S::UW, j = kk / S::UW;
+                float ux = 0.f, uy = 0.f, ir = 0.f;
+                if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny))
+                    flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+                su[kk] = ux;
+                sv[kk] = uy;
+                sir[kk] = ir;
+            }
+        if (!__syncthreads_and(ok)) {
+            // a copy wait ran out: report, let copies in flight land (bounded), stop
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(bar_a + 8u * (unsigned)b, (unsigned)(k >> 1) & 1u);
+                if (t + (int)gridDim.x < ntiles) mbar_wait(bar_a + 8u * (unsigned)(b ^ 1), (unsigned)((k + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        // phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
+        phase2_packed<Dev, Lim, S>(P, tile, su, sv, sir, lane, ty, x0, y0, fout);
+        __syncthreads();
+        if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + 2 * gridDim.x, b);
+        }
+    }
+}
+
+bool tma_pipe_supported(const Params &P)
+{
+    return P.pitch >= kTmaTX + 8 && P.ny + 4 >= TmaPipeShape::SH && P.nx >= kTmaTX;
+}
+
+cudaError_t launch_step_tma_pipe(const Params &P, const void *tmap, void *fout, int *err, cudaStream_t st)
+{
+    const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
+    using S = TmaPipeShape;
+    const void *fn = P.limiter == 0 ? (const void *)k_step_tma_pipe<true, 0>
+                     : P.limiter == 1 ? (const void *)k_step_tma_pipe<true, 1>
+                                      : (const void *)k_step_tma_pipe<true, 2>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTmaTX * kTmaTT, S::smem_bytes);
+    const int ntiles = ((P.nx + kTmaTX - 1) / kTmaTX) * ((P.ny + S::TR - 1) / S::TR);
+    int grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (grid > ntiles) grid = ntiles;
+    const dim3 block(kTmaTX, kTmaTT);
+    float *b = (float *)fout;
+    if (P.limiter == 0) k_step_tma_pipe<true, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
+    else if (P.limiter == 1) k_step_tma_pipe<true, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
+    else k_step_tma_pipe<true, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
+    return cudaGetLastError();
+}
+
+cudaError_t tma_pipe_prepare()
+{
+    cudaError_t e = cudaSuccess;
+    for (const void *fn : {(const void *)k_step_tma_pipe<true, 0>, (const void *)k_step_tma_pipe<true, 1>,
+                           (const void *)k_step_tma_pipe<true, 2>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaPipeShape::smem_bytes);
+    return e;
 }
 
 // ---------------------------------------------------------------------------

@@ -77,14 +77,19 @@ template <int Lim>
 __device__ __forceinline__ float2 slope2x2(float2 a, float2 b)
 {
     if (Lim == 2) return f2(0.f, 0.f);
-    if (Lim == 1) return __fmul2_rn(b, f2(2.f, 2.f));
-    const float2 s = __fadd2_rn(a, b);
+    if (Lim == 1) return mul2(b, f2(2.f, 2.f));
+    // as mc2(float), per lane: t = +-min(|a|, |b|), positive when a and b agree in sign;
+    // the result carries the sign of a + b and the magnitude min(4 max(t, 0), |a + b|)
+    const float2 s = add2(a, b);
     float tx, ty;
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(tx) : "f"(a.x), "f"(b.x));
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(ty) : "f"(a.y), "f"(b.y));
-    const float2 t4 = __fmul2_rn(f2(tx, ty), f2(4.f, 4.f));
-    const float rx = fmaxf(fminf(t4.x, fabsf(s.x)), 0.f), ry = fmaxf(fminf(t4.y, fabsf(s.y)), 0.f);
-    return f2(copysignf(rx, b.x), copysignf(ry, b.y));
+    const float2 t4 = mul2(f2(tx, ty), f2(4.f, 4.f));
+    const float mx = fmaxf(t4.x, 0.f), my = fmaxf(t4.y, 0.f);
+    float rx, ry;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(rx) : "f"(mx), "f"(s.x));
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(ry) : "f"(my), "f"(s.y));
+    return f2(rx, ry);
 }
 
 // (F_out - F_in) of a pair in upwind order (f_{J-2s}, f_{J-s}, f_J, f_{J+s}); hh = h/2 per member.

@@ -392,5 +392,5 @@ class Solver:
 
     @property
     def step_kernel(self):
-        """lbm_options.step_kernel code of the fused-step kernel in use (1 .. 5)."""
+        """lbm_options.step_kernel code of the fused-step kernel in use (1 .. 6)."""
         return lbm_step_kernel(self.h)

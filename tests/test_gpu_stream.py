@@ -1,4 +1,5 @@
-"""GPU parity of the streaming step kernel (lbm_options.step_kernel = 5).
+"""GPU parity of the streaming step kernel (lbm_options.step_kernel = 5) and of the
+persistent double-buffered TMA-staged kernel (step_kernel = 6, float32 only).
 
 The kernel splits strips (256 columns) x rows evenly over its CTAs; a CTA's
 range of rows may end inside one strip and continue at the top of the next, and
@@ -131,3 +132,26 @@ def test_stream_no_copy_wait_ran_out(lbm):
     rho, u, v, T = s.moments()
     s.close()
     assert np.isfinite(rho).all() and np.isfinite(T).all()
+
+
+# ------------------------------------------------ persistent double-buffered TMA-staged kernel
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+@pytest.mark.parametrize("nx,ny", [(150, 70), (32, 16), (61, 45), (600, 40), (1030, 33)])
+def test_pipe_matches_plain(lbm, limiter, nx, ny):
+    p = _crop(wl.shear_layer(max(nx, ny), seed=4, steps=40), nx, ny)
+    a = _state_after(lbm, p, 40, 1, 1, limiter)
+    b = _state_after(lbm, p, 40, 1, 6, limiter)
+    _assert_roundoff(b, a, 1)
+
+
+def test_pipe_matches_plain_walls(lbm):
+    p = _walls(_crop(wl.shear_layer(300, ny=45), 290, 45))
+    a = _state_after(lbm, p, 80, 1, 1)
+    b = _state_after(lbm, p, 80, 1, 6)
+    _assert_roundoff(b, a, 1)
+
+
+def test_pipe_is_float32_only(lbm):
+    p = wl.shock_interface(nx=150, ny=70, steps=1)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter, p.bc, precision=0, step_kernel=6)
