@@ -258,9 +258,10 @@ bool make_tensor_map(CUtensorMap *tm, void *base, const Params &P, int prec, int
 
 bool make_tile_maps(lbm_ctx *c)
 {
-    using S = lbm::TmaShape<float>;
-    return make_tensor_map(&c->tmap[0], c->f[0], c->P, c->prec, S::SW, S::SH) &&
-           make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec, S::SW, S::SH);
+    const int sw = lbm::TmaShape<float>::SW;
+    const int sh = c->prec == LBM_FP32_DEV ? lbm::TmaShape<float>::SH : lbm::TmaShape<double>::SH;
+    return make_tensor_map(&c->tmap[0], c->f[0], c->P, c->prec, sw, sh) &&
+           make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec, sw, sh);
 }
 
 bool make_row_maps(lbm_ctx *c)
@@ -285,7 +286,7 @@ bool stream_ready(lbm_ctx *c)
 
 bool tma_ready(lbm_ctx *c)
 {
-    return lbm::tma_supported(c->P) && lbm::tma_prepare() == cudaSuccess && make_tile_maps(c);
+    return lbm::tma_supported(c->P, c->prec) && lbm::tma_prepare() == cudaSuccess && make_tile_maps(c);
 }
 
 cudaError_t launch_fused_step(lbm_ctx *c)

@@ -45,21 +45,26 @@ cudaError_t launch_unpack(const Params &P, int prec, void *f, int row0, int rows
                           cudaStream_t st);
 
 // TMA-staged step kernel: tiles of kTmaTX columns by TmaShape<R>::TR rows,
-// kTmaTX x kTmaTT threads, each thread owns KR consecutive rows of one column.
+// kTmaTX x TT threads, each thread owns KR consecutive rows of one column.
+// float32: 4 warps and 32 x 16 tiles (four CTAs per SM, so four tile copies in
+// flight); the staged flow velocity is (u_x, u_y) pairs and 1/rho is recomputed
+// from the cell's own density.  float64: 8 warps and 32 x 32 tiles, u_x, u_y and
+// 1/rho staged.
 constexpr int kTmaTX = 32;
 constexpr int kTmaTT = 8;
 template <typename R>
 struct TmaShape {
+    static constexpr int TT = sizeof(R) == sizeof(float) ? 4 : 8;   // warps per CTA
     static constexpr int KR = 4;                       // rows per thread
-    static constexpr int TR = kTmaTT * KR;             // tile rows
+    static constexpr int TR = TT * KR;                 // tile rows
     static constexpr int SW = kTmaTX + 8;              // staged row: x halo of 4 (16-byte TMA origin)
     static constexpr int SH = TR + 4;                  // staged rows: y halo of 2
     static constexpr int PL = SW * SH;                 // staged plane (float32: plane of pairs, in pairs)
     static constexpr int UW = kTmaTX + 2, UH = TR + 2; // flow-velocity tile with its ring
     static constexpr size_t tile_bytes = sizeof(R) * NQ * PL;
-    static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * 3 * UW * UH;
+    static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * (sizeof(R) == sizeof(float) ? 2 : 3) * UW * UH;
 };
-bool tma_supported(const Params &P);
+bool tma_supported(const Params &P, int prec);
 cudaError_t tma_prepare();   // opt the kernels in to their dynamic shared memory (once per device)
 // `tmap` points to the CUtensorMap of the input buffer (3-D: pitch x (ny+4) x 16).
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);

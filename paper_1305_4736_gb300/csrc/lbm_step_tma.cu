@@ -20,21 +20,12 @@
 
 namespace lbm {
 
-namespace {
-
-__device__ __forceinline__ bool tu_cell(int x, int y, int nx, int ny)
-{
-    return (x >= -1 && x <= nx && y >= 0 && y < ny) || (y >= -1 && y <= ny && x >= 0 && x < nx);
-}
-
-}  // namespace
 
 // Phase 2 of the float32 kernel on population pairs: the staged tile is 8 planes of
 // pairs (pair_q(pr), pair_q(pr) + 4), read and written one pair per access.
 template <bool Dev, int Lim, typename S = TmaShape<float>>
-__device__ __forceinline__ void phase2_packed(const Params &P, const float2 *tile, const float *su, const float *sv,
-                                              const float *sir, int lane, int ty, int x0, int y0,
-                                              float *__restrict__ fout)
+__device__ __forceinline__ void phase2_packed(const Params &P, const float2 *tile, const float2 *suv,
+                                              int lane, int ty, int x0, int y0, float *__restrict__ fout)
 {
     const Coef<float> &C = coef<float>(P);
     const int gx = x0 + lane;
@@ -75,13 +66,11 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
         float drho, jx, jy, de;
         conserved2_of(sh, drho, jx, jy, de);
         const int ui = (r + 1) * S::UW + (lane + 1);
-        const float ir = sir[ui];
-        const float dxux = su[ui + 1] - su[ui - 1];
-        const float dyux = su[ui + S::UW] - su[ui - S::UW];
-        const float dxuy = sv[ui + 1] - sv[ui - 1];
-        const float dyuy = sv[ui + S::UW] - sv[ui - S::UW];
+        const float ir = recip(Dev ? C.rho0 + drho : drho);   // as phase 1 computed it
+        const float2 gx2 = sub2(suv[ui + 1], suv[ui - 1]);           // (d_x u_x, d_x u_y) x 2 dx
+        const float2 gy2 = sub2(suv[ui + S::UW], suv[ui - S::UW]);   // (d_y u_x, d_y u_y) x 2 dx
         float2 acc[8];
-        collide2<Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+        collide2<Dev>(P, sh, drho, jx, jy, de, ir, gx2.x, gy2.x, gx2.y, gy2.y, acc);
         const bool store = gx < P.nx && gy < P.ny;
         const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
 #pragma unroll
@@ -117,7 +106,7 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
 }
 
 template <typename R, bool Dev, int Lim>
-__global__ void __launch_bounds__(kTmaTX * kTmaTT, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kTmaTX * TmaShape<R>::TT, sizeof(R) == 4 ? 4 : 1)
 k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, R *__restrict__ fout,
            int *err)
 {
@@ -126,12 +115,12 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     R *tile = reinterpret_cast<R *>(smraw);
     R *su = tile + NQ * S::PL;
     R *sv = su + S::UW * S::UH;
-    R *sir = sv + S::UW * S::UH;
+    R *sir = sv + S::UW * S::UH;   // float64 only
     __shared__ __align__(8) unsigned long long bar;
 
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
-    const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * S::TR;
     const int nx = P.nx, ny = P.ny;
+    const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * S::TR;
     const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
@@ -148,32 +137,47 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0), "r"(y0), "r"(0),
                      "r"(bar_a) : "memory");
     }
-    if (!mbar_wait(bar_a, 0)) {
-        if (tid == 0) atomicExch(err, 1);
-        mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
+    const bool ok = mbar_wait(bar_a, 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
+        }
         return;
     }
-
     const Coef<R> &C = coef<R>(P);
-    // ---- phase 1: flow velocity and 1/rho on the tile plus its ring
-    for (int k = tid; k < S::UW * S::UH; k += kTmaTX * kTmaTT) {
-        const int i = k % S::UW, j = k / S::UW;
-        R ux = R(0), uy = R(0), ir = R(0);
-        if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny)) {
-            if constexpr (sizeof(R) == sizeof(float))
-                flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
-            else
-                flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+    // ---- phase 1: flow velocity and 1/rho on the tile plus its ring.  Cells of the ring
+    // outside the domain's cross (corners, beyond the ghost layer) get values that only
+    // lanes whose results are not stored read.
+    constexpr int kStep = kTmaTX * S::TT;
+    int i = tid % S::UW, j = tid / S::UW;
+    for (int k = tid; k < S::UW * S::UH; k += kStep) {
+        R ux, uy, ir;
+        if constexpr (sizeof(R) == sizeof(float))
+            flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + 3), S::PL, ux, uy,
+                         ir);
+        else
+            flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+        i += kStep % S::UW;
+        j += kStep / S::UW;
+        if (i >= S::UW) {
+            i -= S::UW;
+            j++;
         }
-        su[k] = ux;
-        sv[k] = uy;
-        sir[k] = ir;
+        if constexpr (sizeof(R) == sizeof(float)) {
+            reinterpret_cast<float2 *>(su)[k] = f2(ux, uy);   // float32: (u_x, u_y) pairs
+        } else {
+            su[k] = ux;
+            sv[k] = uy;
+            sir[k] = ir;
+        }
     }
     __syncthreads();
 
     // ---- phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
     if constexpr (sizeof(R) == sizeof(float)) {
-        phase2_packed<Dev, Lim>(P, reinterpret_cast<const float2 *>(tile), su, sv, sir, lane, ty, x0, y0, fout);
+        phase2_packed<Dev, Lim>(P, reinterpret_cast<const float2 *>(tile), reinterpret_cast<const float2 *>(su),
+                                lane, ty, x0, y0, fout);
     } else {
         const int gx = x0 + lane;
         const int r0 = ty * S::KR;
@@ -277,9 +281,7 @@ k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtens
     using S = TmaPipeShape;
     extern __shared__ __align__(128) unsigned char smraw[];
     float2 *buf = reinterpret_cast<float2 *>(smraw);
-    float *su = reinterpret_cast<float *>(smraw + 2 * S::buf_bytes);
-    float *sv = su + S::UW * S::UH;
-    float *sir = sv + S::UW * S::UH;
+    float2 *suv = reinterpret_cast<float2 *>(smraw + 2 * S::buf_bytes);   // (u_x, u_y)
     __shared__ __align__(8) unsigned long long bar[2];
 
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
@@ -318,27 +320,33 @@ k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtens
         const float2 *tile = buf + b * (int)(S::buf_bytes / sizeof(float2));
         const int x0 = (t % ntx) * kTmaTX, y0 = (t / ntx) * S::TR;
         // phase 1: flow velocity and 1/rho on the tile plus its ring
-        if (ok)
-            for (int kk = tid; kk < S::UW * S::UH; kk += kTmaTX * kTmaTT) {
-                const int i = kk % S::UW, j = kk / S::UW;
-                float ux = 0.f, uy = 0.f, ir = 0.f;
-                if (tu_cell(x0 - 1 + i, y0 - 1 + j, nx, ny))
-                    flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
-                su[kk] = ux;
-                sv[kk] = uy;
-                sir[kk] = ir;
+        if (ok) {
+            constexpr int kStep = kTmaTX * kTmaTT;
+            int i = tid % S::UW, j = tid / S::UW;
+            for (int kk = tid; kk < S::UW * S::UH; kk += kStep) {
+                float ux, uy, ir;
+                flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+                suv[kk] = f2(ux, uy);
+                i += kStep % S::UW;
+                j += kStep / S::UW;
+                if (i >= S::UW) {
+                    i -= S::UW;
+                    j++;
+                }
             }
+        }
         if (!__syncthreads_and(ok)) {
             // a copy wait ran out: report, let copies in flight land (bounded), stop
             if (tid == 0) {
                 atomicExch(err, 1);
                 mbar_wait(bar_a + 8u * (unsigned)b, (unsigned)(k >> 1) & 1u);
-                if (t + (int)gridDim.x < ntiles) mbar_wait(bar_a + 8u * (unsigned)(b ^ 1), (unsigned)((k + 1) >> 1) & 1u);
+                if (t + (int)gridDim.x < ntiles)
+                    mbar_wait(bar_a + 8u * (unsigned)(b ^ 1), (unsigned)((k + 1) >> 1) & 1u);
             }
             return;
         }
         // phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
-        phase2_packed<Dev, Lim, S>(P, tile, su, sv, sir, lane, ty, x0, y0, fout);
+        phase2_packed<Dev, Lim, S>(P, tile, suv, lane, ty, x0, y0, fout);
         __syncthreads();
         if (tid == 0 && t + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -385,17 +393,18 @@ cudaError_t tma_pipe_prepare()
 }
 
 // ---------------------------------------------------------------------------
-bool tma_supported(const Params &P)
+bool tma_supported(const Params &P, int prec)
 {
-    return P.pitch >= kTmaTX + 8 && P.ny + 4 >= TmaShape<float>::SH && P.nx >= kTmaTX;
+    const int sh = prec == 0 ? TmaShape<double>::SH : TmaShape<float>::SH;
+    return P.pitch >= kTmaTX + 8 && P.ny + 4 >= sh && P.nx >= kTmaTX;
 }
 
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st)
 {
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
-    const dim3 block(kTmaTX, kTmaTT);
     if (prec == 0) {
         using S = TmaShape<double>;
+        const dim3 block(kTmaTX, S::TT);
         const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
         double *b = (double *)fout;
         if (P.limiter == 0) k_step_tma<double, false, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
@@ -403,6 +412,7 @@ cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *f
         else k_step_tma<double, false, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
     } else {
         using S = TmaShape<float>;
+        const dim3 block(kTmaTX, S::TT);
         const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
         float *b = (float *)fout;
         if (P.limiter == 0) k_step_tma<float, true, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
