@@ -57,7 +57,8 @@ struct TmaShape {
     static constexpr int TT = sizeof(R) == sizeof(float) ? 4 : 8;   // warps per CTA
     static constexpr int KR = 4;                       // rows per thread
     static constexpr int TR = TT * KR;                 // tile rows
-    static constexpr int SW = kTmaTX + 8;              // staged row: x halo of 4 (16-byte TMA origin)
+    static constexpr int HX = 2;                       // x halo (8-byte elements: 16-byte TMA origin)
+    static constexpr int SW = kTmaTX + 2 * HX;         // staged row
     static constexpr int SH = TR + 4;                  // staged rows: y halo of 2
     static constexpr int PL = SW * SH;                 // staged plane (float32: plane of pairs, in pairs)
     static constexpr int UW = kTmaTX + 2, UH = TR + 2; // flow-velocity tile with its ring
@@ -75,7 +76,8 @@ cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *f
 struct TmaPipeShape {
     static constexpr int KR = 2;
     static constexpr int TR = kTmaTT * KR;
-    static constexpr int SW = kTmaTX + 8;
+    static constexpr int HX = 2;
+    static constexpr int SW = kTmaTX + 2 * HX;
     static constexpr int SH = TR + 4;
     static constexpr int PL = SW * SH;                 // staged plane of pairs, in pairs
     static constexpr int UW = kTmaTX + 2, UH = TR + 2;

@@ -31,7 +31,7 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
     const float2 m1 = f2(-1.f, -1.f);
-    const float2 *col = tile + (lane + 4);
+    const float2 *col = tile + (lane + S::HX);
     // sliding y-window state per y-moving pair: last value, face difference, slope
     float2 yw[8], yd[8], ym[8];
 #pragma unroll
@@ -128,14 +128,15 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     }
     __syncthreads();
     if (tid == 0) {
-        // box origin: interior column x0 - 4 = padded column x0; interior row y0 - 2 = padded row y0
+        // box origin: interior column x0 - HX = padded column x0 + OX - HX; interior row y0 - 2 =
+        // padded row y0
         const unsigned dst = (unsigned)__cvta_generic_to_shared(tile);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
                      "r"((unsigned)S::tile_bytes) : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                      " [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0), "r"(y0), "r"(0),
-                     "r"(bar_a) : "memory");
+                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 + OX - S::HX), "r"(y0),
+                     "r"(0), "r"(bar_a) : "memory");
     }
     const bool ok = mbar_wait(bar_a, 0);
     if (!__syncthreads_and(ok)) {
@@ -154,10 +155,10 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
     for (int k = tid; k < S::UW * S::UH; k += kStep) {
         R ux, uy, ir;
         if constexpr (sizeof(R) == sizeof(float))
-            flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + 3), S::PL, ux, uy,
-                         ir);
+            flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux,
+                         uy, ir);
         else
-            flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+            flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux, uy, ir);
         i += kStep % S::UW;
         j += kStep / S::UW;
         if (i >= S::UW) {
@@ -187,7 +188,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         for (int q = 0; q < NQ; q++) {
             const int sy = tsgn_y(q);
             if (sy == 0) continue;
-            const R *pc = tile + q * S::PL + (lane + 4);
+            const R *pc = tile + q * S::PL + (lane + S::HX);
             // window index m <-> smem row r0 + m (tile row r0 + m - 2); D[m] = w[m+1] - w[m]
             if (sy > 0) {
                 // oriented slope at index c: slope2(D[c-1], D[c]); carry w[2], D[1], slope at index 1
@@ -210,7 +211,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         for (int k = 0; k < S::KR; k++) {
             const int r = r0 + k;
             const int gy = y0 + r;
-            const R *p = tile + (r + 2) * S::SW + (lane + 4);
+            const R *p = tile + (r + 2) * S::SW + (lane + S::HX);
             R f[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; q++) f[q] = p[q * S::PL];
@@ -241,7 +242,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                     tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, hh);
                 }
                 if (sy != 0) {
-                    const R *pc = tile + q * S::PL + (lane + 4);
+                    const R *pc = tile + q * S::PL + (lane + S::HX);
                     // next window value: smem row r0 + k + 3 (sy > 0) or r0 + k + 4 (sy < 0)
                     const R wn = pc[(r + (sy > 0 ? 3 : 4)) * S::SW];
                     const R dn = wn - yw[q];
@@ -290,9 +291,9 @@ k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtens
     const int ntiles = ntx * ((ny + S::TR - 1) / S::TR);
     const unsigned bar_a = (unsigned)__cvta_generic_to_shared(bar);
     const unsigned buf_a = (unsigned)__cvta_generic_to_shared(buf);
-    // copy of tile t (box origin: interior (x0 - 4, y0 - 2) = padded (x0, y0)) into buffer b
+    // copy of tile t (box origin: interior (x0 - HX, y0 - 2) = padded (x0 + OX - HX, y0)) into buffer b
     auto issue = [&](int t, int b) {
-        const int x0 = (t % ntx) * kTmaTX, y0 = (t / ntx) * S::TR;
+        const int x0 = (t % ntx) * kTmaTX + OX - S::HX, y0 = (t / ntx) * S::TR;
         const unsigned bb = bar_a + 8u * (unsigned)b;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb),
                      "r"((unsigned)S::buf_bytes) : "memory");
@@ -325,7 +326,7 @@ k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtens
             int i = tid % S::UW, j = tid / S::UW;
             for (int kk = tid; kk < S::UW * S::UH; kk += kStep) {
                 float ux, uy, ir;
-                flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + 3), S::PL, ux, uy, ir);
+                flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux, uy, ir);
                 suv[kk] = f2(ux, uy);
                 i += kStep % S::UW;
                 j += kStep / S::UW;
@@ -357,7 +358,7 @@ k_step_tma_pipe(const __grid_constant__ Params P, const __grid_constant__ CUtens
 
 bool tma_pipe_supported(const Params &P)
 {
-    return P.pitch >= kTmaTX + 8 && P.ny + 4 >= TmaPipeShape::SH && P.nx >= kTmaTX;
+    return P.pitch >= TmaPipeShape::SW && P.ny + 4 >= TmaPipeShape::SH && P.nx >= kTmaTX;
 }
 
 cudaError_t launch_step_tma_pipe(const Params &P, const void *tmap, void *fout, int *err, cudaStream_t st)
@@ -396,7 +397,7 @@ cudaError_t tma_pipe_prepare()
 bool tma_supported(const Params &P, int prec)
 {
     const int sh = prec == 0 ? TmaShape<double>::SH : TmaShape<float>::SH;
-    return P.pitch >= kTmaTX + 8 && P.ny + 4 >= sh && P.nx >= kTmaTX;
+    return P.pitch >= TmaShape<float>::SW && P.ny + 4 >= sh && P.nx >= kTmaTX;
 }
 
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st)
