@@ -415,35 +415,39 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Totals are linear in f: pass 1 sums every population over the cells (in a fixed
-// grid-stride order; in float32 storage, runs of 32 cells are summed in float32 and
-// flushed into float64 accumulators), pass 2 adds the block sums in a fixed order
-// and takes the conserved moments (rho, j, e) of the 16 population totals.
+// Totals are linear in f: pass 1 sums every population over the cells (blocks over rows,
+// threads along each row, in a fixed order; in float32 storage each thread's runs of up to
+// 32 cells are summed in float32 and flushed into float64 accumulators), pass 2 adds the
+// block sums in a fixed order and takes the conserved moments (rho, j, e) of the 16
+// population totals.
 template <typename R, bool Dev>
 __global__ void __launch_bounds__(kTotalsThreads)
 k_totals_partial(const __grid_constant__ Params P, const R *__restrict__ f, double *partial)
 {
     __shared__ double red[kTotalsThreads / 32][NQ];
-    const long long n = (long long)P.nx * P.ny;
     double a[NQ];
-    R run[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; q++) { a[q] = 0.0; run[q] = R(0); }
-    int cnt = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % P.nx), y = (int)(i / P.nx);
-        const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+    for (int q = 0; q < NQ; q++) a[q] = 0.0;
+    for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
+        const long long row = (long long)(y + OY) * P.pitch + OX;
+        R run[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; q++) run[q] += f[pidx<R>(q, P.plane, c)];
-        if (sizeof(R) == sizeof(double) || ++cnt == 32) {
+        for (int q = 0; q < NQ; q++) run[q] = R(0);
+        int cnt = 0;
+        for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
+            R g[NQ];
+            load16(f, P.plane, row + x, g);
 #pragma unroll
-            for (int q = 0; q < NQ; q++) { a[q] += (double)run[q]; run[q] = R(0); }
-            cnt = 0;
+            for (int q = 0; q < NQ; q++) run[q] += g[q];
+            if (sizeof(R) == sizeof(double) || ++cnt == 32) {
+#pragma unroll
+                for (int q = 0; q < NQ; q++) { a[q] += (double)run[q]; run[q] = R(0); }
+                cnt = 0;
+            }
         }
-    }
 #pragma unroll
-    for (int q = 0; q < NQ; q++) a[q] += (double)run[q];
+        for (int q = 0; q < NQ; q++) a[q] += (double)run[q];
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
