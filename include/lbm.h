@@ -103,15 +103,21 @@ typedef struct {
                                       128 columns), 6 = persistent TMA-staged 32 x 16 tiles with
                                       two tile buffers per CTA (LBM_FP32_DEV only); all agree to
                                       round-off (see lbm_autotune) */
+    double dy;                     /* grid spacing along y; <= 0 means dy = dx.  The y projection
+                                      of the convection uses the Courant numbers |v_iy| dt / dy and
+                                      the y derivatives of the energy-flux correction divide by
+                                      2 dy (Sec. III, Sec. II) */
 } lbm_options;
 
 typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
 
-/* Create a problem: grid nx x ny (>= 1), spacing dx (= dy) > 0, time step dt > 0,
-   gamma > 1, Prandtl number Pr > 0, rates s[16], limiter, boundary kinds.
+/* Create a problem: grid nx x ny (>= 1), spacing dx > 0 (dy = dx; lbm_create_ex takes
+   dy in lbm_options), time step dt > 0, gamma > 1, Prandtl number Pr > 0, rates s[16],
+   limiter, boundary kinds.
    s[7] (s_8) <= 0 means s_8 = s_9 = Pr s_5; otherwise |s_8/s_5 - Pr| must be <= 1e-12 Pr.
    Isotropy s_5 = s_6 = s_7 and s_8 = s_9 is required (Sec. II).
-   Errors: LBM_ERR_ARG, LBM_ERR_CFL, LBM_ERR_STABILITY, LBM_ERR_OOM, LBM_ERR_CUDA.
+   Errors: LBM_ERR_ARG, LBM_ERR_CFL (6 dt > min(dx, dy): a Courant number above 1),
+   LBM_ERR_STABILITY, LBM_ERR_OOM, LBM_ERR_CUDA.
    On success *out receives the context (FP64, legacy default stream, cudaMalloc). */
 int lbm_create(int nx, int ny, double dx, double dt, double gamma, double Pr,
                const double s[16], int limiter, const lbm_bc *bc, lbm_ctx **out);

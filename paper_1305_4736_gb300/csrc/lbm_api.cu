@@ -51,7 +51,7 @@ struct lbm_ctx {
     CUtensorMap pmap[2];          // tile-copy descriptors of the double-buffered kernel
     bool initialized = false;
     long long steps = 0;
-    double dx = 0.0;
+    double dx = 0.0, dy = 0.0;
     // profiling (lbm_profile_begin / lbm_profile_end)
     bool prof = false;
     int prof_max = 0, prof_used = 0;
@@ -353,8 +353,11 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
         return fail(nullptr, LBM_ERR_ARG, "isotropy requires s_5 = s_6 = s_7 and s_8 = s_9 (Sec. II)");
     for (int k = 4; k < 16; k++)
         if (s[k] * dt >= 2.0) return fail(nullptr, LBM_ERR_STABILITY, "s_k dt >= 2 for some k >= 5");
-    // largest velocity component is 6 (shell 2): Courant number 6 dt / dx
-    if (6.0 * dt / dx > 1.0) return fail(nullptr, LBM_ERR_CFL, "Courant number 6 dt/dx exceeds 1");
+    const double dy = (opt && opt->dy > 0.0) ? opt->dy : dx;
+    if (!finite_pos(dy)) return fail(nullptr, LBM_ERR_ARG, "dy must be finite and > 0");
+    // largest velocity component is 6 (shell 2): Courant number 6 dt / min(dx, dy)
+    if (6.0 * dt / (dx < dy ? dx : dy) > 1.0)
+        return fail(nullptr, LBM_ERR_CFL, "Courant number 6 dt/min(dx, dy) exceeds 1");
 
     lbm_ctx *c = new (std::nothrow) lbm_ctx;
     if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
@@ -362,6 +365,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     std::memset(&P, 0, sizeof(P));
     c->prec = prec;
     c->dx = dx;
+    c->dy = dy;
     P.nx = nx;
     P.ny = ny;
     P.pitch = (int)pitch_of(nx);
@@ -392,12 +396,19 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     P.has_c9 = (k8 != 0.0 || k9 != 0.0) ? 1 : 0;
     C.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
     C.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
-    // Courant number per shell: dt / (A_i dx), A_i = 1, 1/6, 1/sqrt2, sqrt2/3 (Sec. III)
+    C.ry = dx / dy;
+    C.g4[0] = 4.0;
+    C.g4[1] = 4.0 * C.ry;
+    C.pad_ = 0.0;
+    // Courant number per shell and axis: dt / (A_i d_alpha), A_i = 1, 1/6, 1/sqrt2, sqrt2/3 (Sec. III)
     const double A[4] = {1.0, 1.0 / 6.0, 1.0 / lbm::kSqrt2, lbm::kSqrt2 / 3.0};
     for (int k = 0; k < 4; k++) {
         C.cr[k] = dt / (A[k] * dx);
         C.ncr[k] = -C.cr[k];
         C.hh[k] = 0.25 * (1.0 - C.cr[k]);
+        C.cry[k] = dt / (A[k] * dy);
+        C.ncry[k] = -C.cry[k];
+        C.hhy[k] = 0.25 * (1.0 - C.cry[k]);
     }
     // the float tables are the float64 tables rounded once
     static_assert(sizeof(lbm::Coef<double>) == 2 * sizeof(lbm::Coef<float>), "Coef layout");
@@ -620,7 +631,7 @@ int lbm_totals(lbm_ctx *c, double out[4])
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "totals before lbm_init / lbm_set_state");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
-    ce = lbm::launch_totals(c->P, c->prec, c->f[c->cur], c->aux, c->tot_out, c->dx * c->dx, c->stream);
+    ce = lbm::launch_totals(c->P, c->prec, c->f[c->cur], c->aux, c->tot_out, c->dx * c->dy, c->stream);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "totals kernel");
     double h[4];
     ce = cudaMemcpyAsync(h, c->tot_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);

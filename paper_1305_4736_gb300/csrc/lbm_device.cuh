@@ -62,6 +62,11 @@ struct Coef {
     // pair p belongs to shell 2p + e; e.g. pEx[p][j] = (cEx[2p][j], cEx[2p+1][j])
     R pA[2][2][2], pEx[2][3][2], pEy[2][3][2], pB1[2][2], pB2[2][2];
     R ncr[4];              // -cr
+    // y projection (dy may differ from dx): Courant number dt / (A_i dy), its h/2 and -cr
+    R cry[4], hhy[4], ncry[4];
+    // the central differences are raw (f_{+1} - f_{-1}); q8, q9 carry 1/(2 dx), so a y
+    // difference is weighted by ry = dx/dy; g4 = (4, 4 ry) for the pair form
+    R g4[2], ry, pad_;
 };
 
 struct EdgeDev {
@@ -352,9 +357,10 @@ __device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R 
     for (int k = 4; k < NQ; k++) D[k] = M.m[k] - q[k];
     if (P.has_c9) {
         const R Pt = Dev ? C.P0 + dP : dP;
-        const R div = dxux + dyuy, shr = dxuy + dyux;
+        // y differences weighted by ry = dx/dy (q8, q9 carry 1/(2 dx))
+        const R div = dxux + C.ry * dyuy, shr = dxuy + C.ry * dyux;
         D[7] += C.q8 * Pt * (ux * (R(4.0) * dxux - C.four_inv_b * div) + R(2.0) * uy * shr);
-        D[8] += C.q9 * Pt * (R(2.0) * ux * shr + uy * (R(4.0) * dyuy - C.four_inv_b * div));
+        D[8] += C.q9 * Pt * (R(2.0) * ux * shr + uy * (C.g4[1] * dyuy - C.four_inv_b * div));
     }
     R S[4], X[4], Y[4], Q[4];
 #pragma unroll
@@ -515,8 +521,8 @@ __device__ __forceinline__ void collide2(const Params &P, const Shells2 &sh, flo
     const float2 D6_14 = sub2(f2(m6, m14), f2(q6, q14));
     if (P.has_c9) {
         // (D8, D9 of the paper's 1-based rows) += (q8, q9) P [u . (4 grad u - (4/b) div u) + 2 u_perp shear]
-        const float div = dxux + dyuy, shr = dxuy + dyux;
-        const float2 g = fma2(f2(4.0f, 4.0f), f2(dxux, dyuy), bc2(-C.four_inv_b * div));
+        const float div = fmaf(C.ry, dyuy, dxux), shr = fmaf(C.ry, dyux, dxuy);   // y weighted by dx/dy
+        const float2 g = fma2(ld2(C.g4), f2(dxux, dyuy), bc2(-C.four_inv_b * div));
         const float2 h = fma2(f2(ux, uy), g, mul2(bc2(2.0f * shr), f2(uy, ux)));
         D7_8 = fma2(mul2(ld2(&C.q8), bc2(Pt)), h, D7_8);
     }

@@ -140,16 +140,17 @@ __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__
         for (int q = 0; q < NQ; q++) {
             const int sx = sgn_x(q), sy = sgn_y(q);
             const int shell = q >> 2;
-            const R hh = C.hh[shell];
             auto at = [&](long long c) { return fin[pidx<R>(q, plane, c)]; };
-            R tx_ = R(0), ty_ = R(0);
-            if (sx != 0) tx_ = flux_diff<R, Lim>(at(c0 - 2 * sx), at(c0 - sx), f[q], at(c0 + sx), hh);
+            // sum over the axes of c_alpha (F_out - F_in) (Courant number and h/2 per axis)
+            R conv = R(0);
+            if (sx != 0)
+                conv = C.cr[shell] * flux_diff<R, Lim>(at(c0 - 2 * sx), at(c0 - sx), f[q], at(c0 + sx), C.hh[shell]);
             if (sy != 0) {
                 const long long sp = (long long)sy * pitch;
-                ty_ = flux_diff<R, Lim>(at(c0 - 2 * sp), at(c0 - sp), f[q], at(c0 + sp), hh);
+                const R ty_ = flux_diff<R, Lim>(at(c0 - 2 * sp), at(c0 - sp), f[q], at(c0 + sp), C.hhy[shell]);
+                conv = sx != 0 ? conv + C.cry[shell] * ty_ : C.cry[shell] * ty_;
             }
-            const R tot = (sx != 0 && sy != 0) ? tx_ + ty_ : (sx != 0 ? tx_ : ty_);
-            fout[pidx<R>(q, plane, c0)] = acc[q] - C.cr[shell] * tot;
+            fout[pidx<R>(q, plane, c0)] = acc[q] - conv;
         }
     }
 }

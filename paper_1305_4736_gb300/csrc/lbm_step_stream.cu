@@ -198,30 +198,33 @@ __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &
         const int sx = tsgn_x(qa), sy = tsgn_y(qa);
         const int sa = qa >> 2;
         const int o = pr * BW;
-        const float2 hh = ld2(&C.hh[sa]);
+        const float2 hy = ld2(&C.hhy[sa]);
         const float2 f0 = fp[pr];
         float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
-        if (sx != 0) tx = flux_diff2<Lim>(s0[o - 2 * sx], s0[o - sx], f0, s0[o + sx], hh);
+        if (sx != 0) tx = flux_diff2<Lim>(s0[o - 2 * sx], s0[o - sx], f0, s0[o + sx], ld2(&C.hh[sa]));
         if (sy != 0) {
             const float2 wn = (sy > 0 ? s1 : s2)[o];
             const float2 dn = sub2(wn, W.w[pr]);
             if (sy > 0) {
                 // flux D(y) + h (slope_y - slope_{y-1})
                 const float2 mn = slope2x2<Lim>(W.d[pr], dn);
-                tyv = Lim == 2 ? W.d[pr] : fma2(hh, sub2(mn, W.m[pr]), W.d[pr]);
+                tyv = Lim == 2 ? W.d[pr] : fma2(hy, sub2(mn, W.m[pr]), W.d[pr]);
                 W.m[pr] = mn;
             } else {
                 // flux -D(y+1) + h (slope_y - slope_{y+1})
                 const float2 nd = mul2(W.d[pr], m1);
                 const float2 mn = slope2x2<Lim>(mul2(dn, m1), nd);
-                tyv = Lim == 2 ? nd : fma2(hh, sub2(W.m[pr], mn), nd);
+                tyv = Lim == 2 ? nd : fma2(hy, sub2(W.m[pr], mn), nd);
                 W.m[pr] = mn;
             }
             W.w[pr] = wn;
             W.d[pr] = dn;
         }
-        const float2 tot = (sx != 0 && sy != 0) ? add2(tx, tyv) : (sx != 0 ? tx : tyv);
-        if (store) out2[pr * plane + cg] = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
+        // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
+        float2 out = sub2(f0, acc[pr]);
+        if (sy != 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+        if (sx != 0) out = fma2(ld2(&C.ncr[sa]), tx, out);
+        if (store) out2[pr * plane + cg] = out;
     }
 }
 
@@ -237,26 +240,29 @@ __device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double>
         const int sx = tsgn_x(q), sy = tsgn_y(q);
         const int shell = q >> 2;
         const int o = q * BW;
-        const double hh = C.hh[shell];
+        const double hy = C.hhy[shell];
         double tx = 0.0, tyv = 0.0;
-        if (sx != 0) tx = flux_diff<double, Lim>(s0[o - 2 * sx], s0[o - sx], f[q], s0[o + sx], hh);
+        if (sx != 0) tx = flux_diff<double, Lim>(s0[o - 2 * sx], s0[o - sx], f[q], s0[o + sx], C.hh[shell]);
         if (sy != 0) {
             const double wn = (sy > 0 ? s1 : s2)[o];
             const double dn = wn - W.w[q];
             if (sy > 0) {
                 const double mn = slope2<double, Lim>(W.d[q], dn);
-                tyv = Lim == 2 ? W.d[q] : W.d[q] + hh * (mn - W.m[q]);
+                tyv = Lim == 2 ? W.d[q] : W.d[q] + hy * (mn - W.m[q]);
                 W.m[q] = mn;
             } else {
                 const double mn = slope2<double, Lim>(-dn, -W.d[q]);
-                tyv = Lim == 2 ? -W.d[q] : -W.d[q] + hh * (W.m[q] - mn);
+                tyv = Lim == 2 ? -W.d[q] : -W.d[q] + hy * (W.m[q] - mn);
                 W.m[q] = mn;
             }
             W.w[q] = wn;
             W.d[q] = dn;
         }
-        const double tot = (sx != 0 && sy != 0) ? tx + tyv : (sx != 0 ? tx : tyv);
-        if (store) fout[q * plane + cg] = (f[q] - acc[q]) - C.cr[shell] * tot;
+        // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
+        double out = f[q] - acc[q];
+        if (sy != 0) out -= C.cry[shell] * tyv;
+        if (sx != 0) out -= C.cr[shell] * tx;
+        if (store) fout[q * plane + cg] = out;
     }
 }
 

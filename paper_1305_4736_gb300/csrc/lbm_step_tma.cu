@@ -78,29 +78,32 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
             const int qa = pair_q(pr);
             const int sx = tsgn_x(qa), sy = tsgn_y(qa);
             const int sa = qa >> 2;
-            const float2 hh = ld2(&C.hh[sa]);
+            const float2 hy = ld2(&C.hhy[sa]);
             const float2 f0 = fp[pr];
             const float2 *pp = p + pr * S::PL;
             float2 tx = f2(0.f, 0.f), tyv = f2(0.f, 0.f);
-            if (sx != 0) tx = flux_diff2<Lim>(pp[-2 * sx], pp[-sx], f0, pp[sx], hh);
+            if (sx != 0) tx = flux_diff2<Lim>(pp[-2 * sx], pp[-sx], f0, pp[sx], ld2(&C.hh[sa]));
             if (sy != 0) {
                 const float2 wn = col[pr * S::PL + (r + (sy > 0 ? 3 : 4)) * S::SW];
                 const float2 dn = sub2(wn, yw[pr]);
                 if (sy > 0) {
                     const float2 mn = slope2x2<Lim>(yd[pr], dn);
-                    tyv = Lim == 2 ? yd[pr] : fma2(hh, sub2(mn, ym[pr]), yd[pr]);
+                    tyv = Lim == 2 ? yd[pr] : fma2(hy, sub2(mn, ym[pr]), yd[pr]);
                     ym[pr] = mn;
                 } else {
                     const float2 nyd = mul2(yd[pr], m1);
                     const float2 mn = slope2x2<Lim>(mul2(dn, m1), nyd);
-                    tyv = Lim == 2 ? nyd : fma2(hh, sub2(ym[pr], mn), nyd);
+                    tyv = Lim == 2 ? nyd : fma2(hy, sub2(ym[pr], mn), nyd);
                     ym[pr] = mn;
                 }
                 yw[pr] = wn;
                 yd[pr] = dn;
             }
-            const float2 tot = (sx != 0 && sy != 0) ? add2(tx, tyv) : (sx != 0 ? tx : tyv);
-            if (store) out2[pr * P.plane + cg] = fma2(ld2(&C.ncr[sa]), tot, sub2(f0, acc[pr]));
+            // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
+            float2 out = sub2(f0, acc[pr]);
+            if (sy != 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+            if (sx != 0) out = fma2(ld2(&C.ncr[sa]), tx, out);
+            if (store) out2[pr * P.plane + cg] = out;
         }
     }
 }
@@ -232,14 +235,14 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
             for (int q = 0; q < NQ; q++) {
                 const int sx = tsgn_x(q), sy = tsgn_y(q);
                 const int shell = q >> 2;
-                const R hh = C.hh[shell];
+                const R hy = C.hhy[shell];
                 R tx = R(0), tyv = R(0);
                 if (sx != 0) {
                     // both slopes from the staged row (sharing the upwind slope with the
                     // neighbouring lane would cost a shuffle plus a boundary-lane fix-up)
                     const R *pr = p + q * S::PL;
                     const R fm2 = pr[-2 * sx], fm1 = pr[-sx], fp1 = pr[sx];
-                    tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, hh);
+                    tx = flux_diff<R, Lim>(fm2, fm1, f[q], fp1, C.hh[shell]);
                 }
                 if (sy != 0) {
                     const R *pc = tile + q * S::PL + (lane + S::HX);
@@ -249,19 +252,22 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                     if (sy > 0) {
                         // D[k+2], slope at J = index k+2; flux D[k+1] + h (slope_J - slope_{J-1})
                         const R mn = slope2<R, Lim>(yd[q], dn);
-                        tyv = Lim == 2 ? yd[q] : yd[q] + hh * (mn - ym[q]);
+                        tyv = Lim == 2 ? yd[q] : yd[q] + hy * (mn - ym[q]);
                         ym[q] = mn;
                     } else {
                         // D[k+3], slope at J - sigma = index k+3; flux -D[k+2] + h (slope_J - slope_{J+1})
                         const R mn = slope2<R, Lim>(-dn, -yd[q]);
-                        tyv = Lim == 2 ? -yd[q] : -yd[q] + hh * (ym[q] - mn);
+                        tyv = Lim == 2 ? -yd[q] : -yd[q] + hy * (ym[q] - mn);
                         ym[q] = mn;
                     }
                     yw[q] = wn;
                     yd[q] = dn;
                 }
-                const R tot = (sx != 0 && sy != 0) ? tx + tyv : (sx != 0 ? tx : tyv);
-                if (store) fout[q * P.plane + cg] = (f[q] - acc[q]) - C.cr[shell] * tot;
+                // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
+                R out = f[q] - acc[q];
+                if (sy != 0) out -= C.cry[shell] * tyv;
+                if (sx != 0) out -= C.cr[shell] * tx;
+                if (store) fout[q * P.plane + cg] = out;
             }
         }
 

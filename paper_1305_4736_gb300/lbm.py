@@ -61,7 +61,7 @@ class Allocator(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rho0", ctypes.c_double), ("T0", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("allocator", ctypes.POINTER(Allocator)),
-                ("device", ctypes.c_int), ("step_kernel", ctypes.c_int)]
+                ("device", ctypes.c_int), ("step_kernel", ctypes.c_int), ("dy", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -290,7 +290,7 @@ class Solver:
 
     def __init__(self, nx, ny, dx, dt, gamma, Pr, s, limiter=LBM_LIMITER_MC, bc=None,
                  precision=LBM_FP64, rho0=1.0, T0=1.0, device=0, stream=None, use_torch_allocator=True,
-                 step_kernel=0):
+                 step_kernel=0, dy=None):
         import torch
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
@@ -302,7 +302,7 @@ class Solver:
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self._keep = []
         opts = Options(int(precision), float(rho0), float(T0), ctypes.c_void_p(handle), None, self.device,
-                       int(step_kernel))
+                       int(step_kernel), float(dy) if dy is not None else 0.0)
         if use_torch_allocator:
             dev = self.device
 
@@ -326,6 +326,7 @@ class Solver:
 
     @classmethod
     def from_problem(cls, p, precision=LBM_FP64, **kw):
+        kw.setdefault("dy", p.dy)
         return cls(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter, p.bc, precision=precision, **kw)
 
     def close(self):

@@ -43,6 +43,7 @@ class Problem:
     steps: int
     limiter: int = LIMITER_MC
     meta: dict = field(default_factory=dict)
+    dy: float | None = None             # grid spacing along y; None: dy = dx
 
     @property
     def cells(self) -> int:
@@ -113,6 +114,29 @@ def sod(nx: int = 200, ny: int = 4, steps: int | None = None) -> Problem:
     if steps is not None:
         p.steps = steps
     return p
+
+
+def discontinuity(nx: int = 1000, ny: int = 4, limiter: int = LIMITER_MC) -> Problem:
+    """The discontinuity test of Sec. IV.A at the paper's parameters: gamma = 2,
+    (rho, u, v, T) = (3/2, 2/3, 0, 14/9) | (1, 0, 0, 1) (the Hugoniot states of a Mach-sqrt2
+    shock moving at speed 2 into gas at rest; the paper prints them rounded), L = 1, dx = dy =
+    1e-3, dt = 1e-5, s5 = s6 = s7 = 5e4 and every other rate 1e5 (so s8 = s9 = 1e5), fixed
+    equilibrium x ends, periodic y, t = 0.06 (6000 steps)."""
+    r2, u2, p2, _ = normal_shock_state(1.0, 1.0, math.sqrt(2.0), 2.0)
+    p = riemann(nx, ny, (r2, u2, 0.0, p2 / r2), (1.0, 0.0, 0.0, 1.0), 2.0, rates(5e4, 1e5, 1e5),
+                length=nx * 1e-3, dt=1e-5, t_end=0.06, limiter=limiter, name="discontinuity",
+                bc_kind=BC_EQUILIBRIUM)
+    return p
+
+
+def lax(nx: int = 1000, ny: int = 4, limiter: int = LIMITER_MC) -> Problem:
+    """The Lax shock tube of Sec. IV.B at the paper's parameters: gamma = 1.4,
+    (rho, u, v, T) = (0.445, 0.698, 0, 7.928) | (0.5, 0, 0, 1.142), dx = dy = 3e-3, dt = 1e-5,
+    s5 = s6 = s7 = 2e3, s8 = s9 = 1e3, other rates 1e5, t = 0.45 (45000 steps).  The paper does
+    not give L; 1000 cells (L = 3, diaphragm at 1.5) keep every wave inside until t = 0.45.
+    Fixed equilibrium x ends, periodic y."""
+    return riemann(nx, ny, (0.445, 0.698, 0.0, 7.928), (0.5, 0.0, 0.0, 1.142), 1.4, rates(2e3, 1e3, 1e5),
+                   length=nx * 3e-3, dt=1e-5, t_end=0.45, limiter=limiter, name="lax", bc_kind=BC_EQUILIBRIUM)
 
 
 def couette(Pr: float = 1.0, nx: int = 4, ny: int = 200, dx: float | None = None,

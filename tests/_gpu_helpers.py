@@ -5,11 +5,11 @@ import numpy as np
 def run_both(orc, lbm, p, steps, precision=0, limiter=None):
     """Run problem p for `steps` on the GPU (through the C interface) and on the oracle."""
     lim = p.limiter if limiter is None else limiter
-    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, lim, p.bc, precision=precision)
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, lim, p.bc, precision=precision, dy=p.dy)
     s.init(*p.fields())
     if steps:
         s.step(steps)
-    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, lim, p.bc)
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, lim, p.bc, dy=p.dy)
     O.init(*p.fields())
     if steps:
         O.step(steps)
