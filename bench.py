@@ -59,7 +59,7 @@ def parse_args(argv=None):
                     help="precisions to measure (the headline line is FP32 unless --mode f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", type=int, default=0,
-                    help="lbm_options.step_kernel (0 = automatic, 1/3/4 plain, 2 TMA tiles, 5 streaming, "
+                    help="lbm_options.step_kernel (0 = automatic, 1/3/4/7 plain, 2 TMA tiles, 5 streaming, "
                          "6 double-buffered TMA tiles)")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests of the serving measurement (0 = skip)")
@@ -172,8 +172,9 @@ def pinned_like(a):
 
 
 # ------------------------------------------------------------------------- GPU arm
-KERNEL_NAMES = {1: "k_step<{r},{d},MC,8>", 2: "k_step_tma<{r},{d},MC>", 3: "k_step<{r},{d},MC,4>",
-                4: "k_step<{r},{d},MC,16>", 5: "k_step_stream<{r},{d},MC>", 6: "k_step_tma_pipe<{r},{d},MC>"}
+KERNEL_NAMES = {1: "k_step<{r},{d},MC,256>", 2: "k_step_tma<{r},{d},MC>", 3: "k_step<{r},{d},MC,128>",
+                4: "k_step<{r},{d},MC,512>", 5: "k_step_stream<{r},{d},MC>", 6: "k_step_tma_pipe<{r},{d},MC>",
+                7: "k_step<{r},{d},MC,64>"}
 
 
 def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):

@@ -93,16 +93,21 @@ typedef struct {
     void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
-    int step_kernel;               /* fused-step kernel: 0 = automatic (float64: streaming, float32:
-                                      TMA-staged, where the grid allows; else the other, else
-                                      plain 32 x 8), 1 = plain 32 x 8 tiles
+    int step_kernel;               /* fused-step kernel: 0 = automatic (float64: streaming on grids
+                                      that give every SM at least 32 rows of a 256-column strip
+                                      and have at least 4M cells, else plain 64-cell tiles;
+                                      float32: TMA-staged where the grid allows, else plain
+                                      32 x 8), 1 = plain 32 x 8 tiles (grids narrower than 32
+                                      columns: TX x NT/TX tiles of the same NT threads, TX the
+                                      smallest power of two >= nx, for options 1, 3, 4, 7)
                                       (global-memory stencil), 2 = TMA-staged 32 x 32 tiles (grids of
                                       at least 32 x 32), 3 = plain 32 x 4, 4 = plain 32 x 16,
                                       5 = streaming (CTAs walk 256-column strips row by row
                                       through a ring of TMA-filled row slots; grids of at least
                                       128 columns), 6 = persistent TMA-staged 32 x 16 tiles with
-                                      two tile buffers per CTA (LBM_FP32_DEV only); all agree to
-                                      round-off (see lbm_autotune) */
+                                      two tile buffers per CTA (LBM_FP32_DEV only), 7 = plain
+                                      64-cell tiles (32 x 2; spreads small float64 grids over
+                                      every SM); all agree to round-off (see lbm_autotune) */
     double dy;                     /* grid spacing along y; <= 0 means dy = dx.  The y projection
                                       of the convection uses the Courant numbers |v_iy| dt / dy and
                                       the y derivatives of the energy-flux correction divide by
@@ -177,7 +182,7 @@ int lbm_profile_end(lbm_ctx *ctx, double out[4]);
 int lbm_peak_fp64(int device, double *flops);
 
 /* Pick the fastest fused-step kernel for this context's grid: times `reps` launches of
-   each candidate (plain 32 x 4, 32 x 8, 32 x 16 tiles; TMA-staged 32 x 32 tiles, the
+   each candidate (plain 32 x 4, 32 x 8, 32 x 16 and 64-cell tiles; TMA-staged tiles, the
    streaming kernel and the double-buffered TMA-staged kernel when the grid and precision
    allow) on the context's current state, writing the spare buffer without advancing the
    state, and keeps the fastest for later lbm_step calls.  *choice (may be NULL) receives
@@ -190,7 +195,9 @@ int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
    steps are launch-bound.  The contexts must be initialised, share one device and one
    stream, and stay alive while the batch exists.  Each step of lbm_batch_step runs, per
    group of contexts with the same precision and limiter, one batched ghost-fill launch
-   and one fused-step launch whose persistent CTAs walk a tile list (32 x 8 tiles) across
+   and one fused-step launch whose persistent CTAs walk a tile list (float32: 256-cell tiles,
+   float64: 64-cell tiles, which spread small float64 grids over more SMs; 32 columns wide,
+   or TX = the smallest power of two >= nx for narrower grids) across
    the group's grids; the arithmetic per cell is that of the plain step kernel.  Pairs of
    steps are replayed from a CUDA graph captured on the first call with n >= 2.
    Results agree with stepping each context alone to round-off (the batched kernel reads
@@ -230,7 +237,7 @@ int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream,
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* The lbm_options.step_kernel code (1 .. 6) of the fused-step kernel this context runs
+/* The lbm_options.step_kernel code (1 .. 7) of the fused-step kernel this context runs
    (after automatic selection or lbm_autotune); -1 for a NULL context. */
 int lbm_step_kernel(const lbm_ctx *ctx);
 

@@ -470,13 +470,30 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->tot_out = c->aux + lbm::kTotalsBlocks * NQ;
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
-    const int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 6) {
+    int want = opt ? opt->step_kernel : 0;
+    if (want < 0 || want > 7) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
     if (want == 3) c->plain_ty = 4;
     if (want == 4) c->plain_ty = 16;
+    if (want == 7) c->plain_ty = 2;
+    // automatic, float64 (bound by the float64 pipe, about 1.6 lane operations per cycle per
+    // SM on GB300): the streaming kernel when the grid gives every SM at least 32 rows of a
+    // 256-column strip; else the plain kernel, on 256-cell tiles when they still give every SM
+    // four tiles (their flow-velocity ring costs less), on 64-cell tiles below that, which
+    // spread a small grid's float64 work over more SMs
+    if (want == 0 && prec == LBM_FP64) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (sms < 1) sms = 152;
+        const long long strips = (nx + lbm::StreamShape<double>::W - 1) / lbm::StreamShape<double>::W;
+        const long long cells = (long long)nx * ny;
+        if (strips * ny < 32LL * sms || cells < (4LL << 20)) {
+            want = cells >= 4LL * lbm::kBatchThreads * sms ? 1 : 7;
+            c->plain_ty = want == 7 ? 2 : lbm::kTY;
+        }
+    }
     // automatic: float64 runs the streaming kernel (fewer float64 operations per cell), float32
     // the TMA-staged tile kernel (fewer instructions per cell); each falls back to the other
     // and then to the plain kernel where the grid or driver does not allow it
@@ -782,10 +799,10 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "autotune before lbm_init / lbm_set_state");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
-    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 2 = TMA-staged 32x32, 5 = streaming,
-    // 6 = double-buffered TMA-staged 32x16 (float32)
-    int cands[6] = {1, 3, 4, 0, 0, 0};
-    int ncand = 3;
+    // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 7 = plain 64-cell tiles,
+    // 2 = TMA-staged, 5 = streaming, 6 = double-buffered TMA-staged 32x16 (float32)
+    int cands[7] = {1, 3, 4, 7, 0, 0, 0};
+    int ncand = 4;
     const bool tma_ok = c->use_tma || tma_ready(c);
     cudaGetLastError();
     const bool stream_ok = c->use_stream || stream_ready(c);
@@ -813,7 +830,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
             if (cd == 2)
                 return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
             return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream,
-                                    cd == 3 ? 4 : (cd == 4 ? 16 : 8));
+                                    cd == 3 ? 4 : (cd == 4 ? 16 : (cd == 7 ? 2 : 8)));
         };
         ce = run();
         if (ce != cudaSuccess) break;
@@ -831,7 +848,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     c->use_tma = best_c == 2;
     c->use_stream = best_c == 5;
     c->use_pipe = best_c == 6;
-    c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : 8);
+    c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : (best_c == 7 ? 2 : 8));
     if (choice) *choice = best_c;
     return LBM_OK;
 }
@@ -844,7 +861,7 @@ int lbm_step_kernel(const lbm_ctx *c)
     if (c->use_pipe) return 6;
     if (c->use_stream) return 5;
     if (c->use_tma) return 2;
-    return c->plain_ty == 4 ? 3 : (c->plain_ty == 16 ? 4 : 1);
+    return c->plain_ty == 4 ? 3 : (c->plain_ty == 16 ? 4 : (c->plain_ty == 2 ? 7 : 1));
 }
 
 }  // extern "C"
@@ -860,6 +877,7 @@ struct lbm_batch {
         lbm::BatchGrid *dG = nullptr;
         int4 *dT = nullptr;
         int ntiles = 0, max_ghost = 0;
+        int nt = lbm::kBatchThreads;             // threads (= cells) per tile
     };
     std::vector<lbm_ctx *> ctxs;
     std::vector<Group> groups;
@@ -887,7 +905,8 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
     for (auto &g : b->groups) {
         cudaError_t ce = lbm::launch_ghost_batch(g.dP, g.dG, (int)g.members.size(), g.max_ghost, g.prec, phase, st);
         if (ce == cudaSuccess)
-            ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, b->ctas, phase, st);
+            ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
+                                        g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
         if (ce != cudaSuccess) return ce;
     }
     return cudaSuccess;
@@ -934,6 +953,13 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
         g->members.push_back(i);
     }
     for (auto &g : b->groups) {
+        // float64 groups too small to give every SM four 256-cell tiles take 64-cell tiles,
+        // which spread their float64 work over more SMs
+        if (g.prec == LBM_FP64) {
+            long long cells = 0;
+            for (int m : g.members) cells += (long long)b->ctxs[m]->P.nx * b->ctxs[m]->P.ny;
+            g.nt = cells >= 4LL * lbm::kBatchThreads * sms ? lbm::kBatchThreads : lbm::kBatchThreadsFp64;
+        }
         std::vector<int4> tiles;
         std::vector<lbm::Params> hp;
         for (size_t k = 0; k < g.members.size(); k++) {
@@ -941,8 +967,11 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             hp.push_back(c->P);
             g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
-            for (int y = 0; y < c->P.ny; y += lbm::kTY)
-                for (int x = 0; x < c->P.nx; x += lbm::kTX) tiles.push_back(make_int4((int)k, x, y, 0));
+            const int lt = lbm::plain_log_tx(c->P.nx);
+            const int nt = g.nt;
+            const int tw = 1 << lt, th = nt >> lt;
+            for (int y = 0; y < c->P.ny; y += th)
+                for (int x = 0; x < c->P.nx; x += tw) tiles.push_back(make_int4((int)k, x, y, lt));
         }
         g.ntiles = (int)tiles.size();
         // sections start on 256-byte boundaries (the tile list is read as int4)

@@ -21,6 +21,12 @@ cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields
 cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
 // Plain fused step with tiles of 32 x ty cells (ty = 4, 8 or 16).
 cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty = kTY);
+// log2 of the plain kernels' tile width for a grid nx columns wide (5 for nx >= 32, else the
+// smallest power of two >= nx); the tile has (kTX * kTY) >> log rows.
+int plain_log_tx(int nx);
+// threads (= cells) per CTA and tile of the batched step kernel: float32 groups, float64 groups
+constexpr int kBatchThreads = kTX * kTY;
+constexpr int kBatchThreadsFp64 = 64;
 
 // One grid of a batch: its two population buffers and which one holds the current step.
 struct BatchGrid {
@@ -33,7 +39,7 @@ struct BatchGrid {
 cudaError_t launch_ghost_batch(const Params *Pall, const BatchGrid *G, int ngrids, int max_ghost, int prec,
                                int phase, cudaStream_t st);
 cudaError_t launch_step_batch(const Params *Pall, const BatchGrid *G, const int4 *tiles, int ntiles, int prec,
-                              int limiter, int ctas, int phase, cudaStream_t st);
+                              int limiter, int nt, int ctas, int phase, cudaStream_t st);
 cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, int rows,
                            double *rho, double *u, double *v, double *T, double *delta,
                            double *dstar, int *flag, cudaStream_t st);

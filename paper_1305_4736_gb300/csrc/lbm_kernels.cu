@@ -68,16 +68,21 @@ __device__ __forceinline__ void velocity_of(const Params &P, const R *f, R &ux, 
 }
 
 // ---------------------------------------------------------------------------
-// Fused step (plain form): one thread per cell of a 32 x TY tile; the flow
-// velocity of the tile + 1 ring goes through shared memory, the limiter reads
-// its stencil from global memory (L1 / L2).  The tile body is shared by the
-// single-grid kernel and the batched kernel (which walks a tile work list).
+// Fused step (plain form): one thread per cell of a tile of TX x TY cells (TX a power
+// of two, TX * TY = threads per CTA); the flow velocity of the tile + 1 ring goes
+// through shared memory, the limiter reads its stencil from global memory (L1 / L2).
+// Grids narrower than 32 columns use TX = the smallest power of two >= nx, so that
+// every lane of a warp has a cell (GB300's float64 unit charges each warp instruction
+// for all 32 lanes).  The tile body is shared by the single-grid kernel and the
+// batched kernel (which walks a tile work list).
 // ---------------------------------------------------------------------------
-template <typename R, bool Dev, int Lim, int TY>
+template <typename R, bool Dev, int Lim>
 __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__ fin, R *__restrict__ fout,
-                                          int x0, int y0, R (*su)[kTX + 2], R (*sv)[kTX + 2])
+                                          int x0, int y0, int TX, int log_tx, int TY, R *su, R *sv)
 {
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int tx = tid & (TX - 1), ty = tid >> log_tx;
+    const int W = TX + 2;                              // row stride of su, sv
     const int ix = x0 + tx, iy = y0 + ty;
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const long long plane = P.plane;
@@ -93,41 +98,40 @@ __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__
         conserved_of(sh, drho, jx, jy, de);
         const R rho = Dev ? coef<R>(P).rho0 + drho : drho;
         ir = recip(rho);
-        su[ty + 1][tx + 1] = jx * ir;
-        sv[ty + 1][tx + 1] = jy * ir;
+        su[(ty + 1) * W + tx + 1] = jx * ir;
+        sv[(ty + 1) * W + tx + 1] = jy * ir;
     } else if (u_cell(ix, iy, nx, ny)) {
         R g[NQ];
         load16(fin, plane, c0, g);
         R a, b;
         velocity_of<R, Dev>(P, g, a, b);
-        su[ty + 1][tx + 1] = a;
-        sv[ty + 1][tx + 1] = b;
+        su[(ty + 1) * W + tx + 1] = a;
+        sv[(ty + 1) * W + tx + 1] = b;
     }
     // ring of the tile: bottom row, top row, left column, right column
-    const int t = ty * kTX + tx;
-    if (t < 2 * (kTX + TY)) {
+    for (int t = tid; t < 2 * (TX + TY); t += nthreads) {
         int rx, ry, lx, ly;
-        if (t < kTX) { rx = x0 + t; ry = y0 - 1; lx = t + 1; ly = 0; }
-        else if (t < 2 * kTX) { rx = x0 + t - kTX; ry = y0 + TY; lx = t - kTX + 1; ly = TY + 1; }
-        else if (t < 2 * kTX + TY) { rx = x0 - 1; ry = y0 + t - 2 * kTX; lx = 0; ly = t - 2 * kTX + 1; }
-        else { rx = x0 + kTX; ry = y0 + t - 2 * kTX - TY; lx = kTX + 1; ly = t - 2 * kTX - TY + 1; }
+        if (t < TX) { rx = x0 + t; ry = y0 - 1; lx = t + 1; ly = 0; }
+        else if (t < 2 * TX) { rx = x0 + t - TX; ry = y0 + TY; lx = t - TX + 1; ly = TY + 1; }
+        else if (t < 2 * TX + TY) { rx = x0 - 1; ry = y0 + t - 2 * TX; lx = 0; ly = t - 2 * TX + 1; }
+        else { rx = x0 + TX; ry = y0 + t - 2 * TX - TY; lx = TX + 1; ly = t - 2 * TX - TY + 1; }
         if (u_cell(rx, ry, nx, ny)) {
             R g[NQ];
             load16(fin, plane, (long long)(ry + OY) * pitch + (rx + OX), g);
             R a, b;
             velocity_of<R, Dev>(P, g, a, b);
-            su[ly][lx] = a;
-            sv[ly][lx] = b;
+            su[ly * W + lx] = a;
+            sv[ly * W + lx] = b;
         }
     }
     __syncthreads();
     if (inside) {
         // central differences (the 1/(2 dx) factor is folded into q8, q9)
-        const int lx = tx + 1, ly = ty + 1;
-        const R dxux = su[ly][lx + 1] - su[ly][lx - 1];
-        const R dyux = su[ly + 1][lx] - su[ly - 1][lx];
-        const R dxuy = sv[ly][lx + 1] - sv[ly][lx - 1];
-        const R dyuy = sv[ly + 1][lx] - sv[ly - 1][lx];
+        const int k = (ty + 1) * W + tx + 1;
+        const R dxux = su[k + 1] - su[k - 1];
+        const R dyux = su[k + W] - su[k - W];
+        const R dxuy = sv[k + 1] - sv[k - 1];
+        const R dyuy = sv[k + W] - sv[k - W];
 
         R acc[NQ];
         collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
@@ -155,43 +159,56 @@ __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__
     }
 }
 
-template <typename R, bool Dev, int Lim, int TY>
-__global__ void __launch_bounds__(kTX * TY)
-k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restrict__ fout)
+template <typename R, bool Dev, int Lim, int NT>
+__global__ void __launch_bounds__(NT)
+k_step(const __grid_constant__ Params P, const R *__restrict__ fin, R *__restrict__ fout, int TX, int log_tx)
 {
-    __shared__ R su[TY + 2][kTX + 2];
-    __shared__ R sv[TY + 2][kTX + 2];
-    step_tile<R, Dev, Lim, TY>(P, fin, fout, blockIdx.x * kTX, blockIdx.y * TY, su, sv);
+    extern __shared__ __align__(16) unsigned char smem_plain[];
+    const int TY = NT / TX;
+    R *su = reinterpret_cast<R *>(smem_plain);
+    R *sv = su + (TX + 2) * (TY + 2);
+    step_tile<R, Dev, Lim>(P, fin, fout, blockIdx.x * TX, blockIdx.y * TY, TX, log_tx, TY, su, sv);
 }
 
 static_assert(sizeof(Params) % sizeof(int4) == 0, "Params is copied to shared memory as int4 words");
 
-// Batched step: persistent CTAs walk a tile list spanning many grids; each tile
-// names its grid, whose parameter block is copied into shared memory when the
-// grid changes.  `phase` selects which of the two buffers is the input.
-template <typename R, bool Dev, int Lim>
-__global__ void __launch_bounds__(kTX * kTY)
+// Batched step: persistent CTAs of NT threads walk contiguous shares of a tile list spanning
+// many grids; each
+// tile (int4 {grid, x0, y0, log2 TX}) names its grid, whose parameter block is copied into
+// shared memory when the grid changes, and its width (TY = NT / TX).  `phase` selects which
+// of the two buffers is the input.  float64 groups use NT = 64: GB300 executes float64 at
+// about 1.6 lane operations per cycle per SM, so small tiles spread a small grid's work over
+// more SMs; float32 groups use NT = 256.
+template <typename R, bool Dev, int Lim, int NT>
+__global__ void __launch_bounds__(NT)
 k_step_batch(const Params *__restrict__ Pall, const BatchGrid *__restrict__ G, const int4 *__restrict__ tiles,
              int ntiles, int phase)
 {
-    __shared__ R su[kTY + 2][kTX + 2];
-    __shared__ R sv[kTY + 2][kTX + 2];
+    constexpr int kSmem = 3 * (NT + 2);            // max over TX of (TX + 2)(TY + 2), at TX = 1
+    __shared__ R su[kSmem];
+    __shared__ R sv[kSmem];
     __shared__ __align__(16) Params Ps;
     int cur_grid = -1;
-    const int tid = threadIdx.y * kTX + threadIdx.x;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tid = threadIdx.x;
+    // a contiguous share of the tile list per CTA: the tiles of a grid are adjacent in the
+    // list, so a CTA reloads the parameter block about once per grid it touches
+    const int t0 = (int)((long long)ntiles * blockIdx.x / gridDim.x);
+    const int t1 = (int)((long long)ntiles * (blockIdx.x + 1) / gridDim.x);
+    for (int t = t0; t < t1; t++) {
         const int4 tl = tiles[t];
         __syncthreads();                             // the previous tile is done with su, sv, Ps
         if (tl.x != cur_grid) {
             const int4 *src = reinterpret_cast<const int4 *>(Pall + tl.x);
             int4 *dst = reinterpret_cast<int4 *>(&Ps);
-            for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kTX * kTY) dst[k] = src[k];
+            for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += NT) dst[k] = src[k];
             cur_grid = tl.x;
             __syncthreads();
         }
         const BatchGrid g = G[tl.x];
         const int in = g.cur ^ phase;
-        step_tile<R, Dev, Lim, kTY>(Ps, (const R *)g.buf[in], (R *)g.buf[in ^ 1], tl.y, tl.z, su, sv);
+        const int TX = 1 << tl.w;
+        step_tile<R, Dev, Lim>(Ps, (const R *)g.buf[in], (R *)g.buf[in ^ 1], tl.y, tl.z, TX, tl.w, NT / TX, su,
+                               sv);
     }
 }
 
@@ -553,30 +570,45 @@ cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <typename R, bool Dev, int TY>
-static void step_launch_ty(const Params &P, const R *a, R *b, cudaStream_t st)
+// Tile width of the plain kernels for a grid nx columns wide: 32, or the smallest power of
+// two >= nx for narrower grids (log2 returned).
+int plain_log_tx(int nx)
 {
-    const dim3 block(kTX, TY);
-    const dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + TY - 1) / TY);
-    if (P.limiter == 0) k_step<R, Dev, 0, TY><<<grid, block, 0, st>>>(P, a, b);
-    else if (P.limiter == 1) k_step<R, Dev, 1, TY><<<grid, block, 0, st>>>(P, a, b);
-    else k_step<R, Dev, 2, TY><<<grid, block, 0, st>>>(P, a, b);
+    int l = 0;
+    while ((1 << l) < nx && l < 5) l++;
+    return l;
+}
+
+template <typename R, bool Dev, int NT>
+static void step_launch_nt(const Params &P, const R *a, R *b, cudaStream_t st)
+{
+    const int log_tx = plain_log_tx(P.nx);
+    const int TX = 1 << log_tx, TY = NT / TX;
+    const dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    const size_t smem = 2 * sizeof(R) * (TX + 2) * (TY + 2);
+    if (P.limiter == 0) k_step<R, Dev, 0, NT><<<grid, NT, smem, st>>>(P, a, b, TX, log_tx);
+    else if (P.limiter == 1) k_step<R, Dev, 1, NT><<<grid, NT, smem, st>>>(P, a, b, TX, log_tx);
+    else k_step<R, Dev, 2, NT><<<grid, NT, smem, st>>>(P, a, b, TX, log_tx);
 }
 
 cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty)
 {
+    // ty: rows of a 32-column tile (2, 4, 8 or 16: 64 .. 512 threads); grids narrower than
+    // 32 columns keep the thread count with TX = the smallest power of two >= nx
     if (prec == 0) {
         const double *a = (const double *)fin;
         double *b = (double *)fout;
-        if (ty == 4) step_launch_ty<double, false, 4>(P, a, b, st);
-        else if (ty == 16) step_launch_ty<double, false, 16>(P, a, b, st);
-        else step_launch_ty<double, false, 8>(P, a, b, st);
+        if (ty == 2) step_launch_nt<double, false, kTX * 2>(P, a, b, st);
+        else if (ty == 4) step_launch_nt<double, false, kTX * 4>(P, a, b, st);
+        else if (ty == 16) step_launch_nt<double, false, kTX * 16>(P, a, b, st);
+        else step_launch_nt<double, false, kTX * 8>(P, a, b, st);
     } else {
         const float *a = (const float *)fin;
         float *b = (float *)fout;
-        if (ty == 4) step_launch_ty<float, true, 4>(P, a, b, st);
-        else if (ty == 16) step_launch_ty<float, true, 16>(P, a, b, st);
-        else step_launch_ty<float, true, 8>(P, a, b, st);
+        if (ty == 2) step_launch_nt<float, true, kTX * 2>(P, a, b, st);
+        else if (ty == 4) step_launch_nt<float, true, kTX * 4>(P, a, b, st);
+        else if (ty == 16) step_launch_nt<float, true, kTX * 16>(P, a, b, st);
+        else step_launch_nt<float, true, kTX * 8>(P, a, b, st);
     }
     return cudaGetLastError();
 }
@@ -593,19 +625,23 @@ cudaError_t launch_ghost_batch(const Params *Pall, const BatchGrid *G, int ngrid
 }
 
 cudaError_t launch_step_batch(const Params *Pall, const BatchGrid *G, const int4 *tiles, int ntiles, int prec,
-                              int limiter, int ctas, int phase, cudaStream_t st)
+                              int limiter, int nt, int ctas, int phase, cudaStream_t st)
 {
     if (ntiles == 0) return cudaSuccess;
-    const dim3 block(kTX, kTY);
     const int grid = ntiles < ctas ? ntiles : ctas;
-    if (prec == 0) {
-        if (limiter == 0) k_step_batch<double, false, 0><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
-        else if (limiter == 1) k_step_batch<double, false, 1><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
-        else k_step_batch<double, false, 2><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+    constexpr int N64 = kBatchThreadsFp64, N32 = kBatchThreads;
+    if (prec == 0 && nt == N64) {
+        if (limiter == 0) k_step_batch<double, false, 0, N64><<<grid, N64, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else if (limiter == 1) k_step_batch<double, false, 1, N64><<<grid, N64, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else k_step_batch<double, false, 2, N64><<<grid, N64, 0, st>>>(Pall, G, tiles, ntiles, phase);
+    } else if (prec == 0) {
+        if (limiter == 0) k_step_batch<double, false, 0, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else if (limiter == 1) k_step_batch<double, false, 1, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else k_step_batch<double, false, 2, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
     } else {
-        if (limiter == 0) k_step_batch<float, true, 0><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
-        else if (limiter == 1) k_step_batch<float, true, 1><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
-        else k_step_batch<float, true, 2><<<grid, block, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        if (limiter == 0) k_step_batch<float, true, 0, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else if (limiter == 1) k_step_batch<float, true, 1, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
+        else k_step_batch<float, true, 2, N32><<<grid, N32, 0, st>>>(Pall, G, tiles, ntiles, phase);
     }
     return cudaGetLastError();
 }

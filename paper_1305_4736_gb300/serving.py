@@ -69,7 +69,7 @@ class GpuBackend:
         return self.lbm.lbm_footprint(p.nx, p.ny, precision)
 
     def create(self, p, precision):
-        s = self.lbm.Solver.from_problem(p, precision=precision, device=self.device, step_kernel=1)
+        s = self.lbm.Solver.from_problem(p, precision=precision, device=self.device)
         s.init(*p.fields())
         return s
 

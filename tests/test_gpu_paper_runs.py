@@ -7,14 +7,16 @@
   (Lax-Wendroff) the shocked region oscillates, the overshoot being more than 20 times
   the MC one (the paper's comparison of Fig. 3).  The GPU run matches the oracle at the
   full 6000 steps (1e-10).
-- Lax shock tube (Sec. IV.B, workloads.lax: dx = 3e-3, dt = 1e-5, t = 0.45, 45000
-  steps): the GPU result follows the exact Riemann solution (mean absolute errors of
-  rho, u, p below 0.02; the oracle gives 0.0157, 0.0114, 0.0120 on the same run), and it
-  matches the oracle over the first 500 steps (1e-10).  At this temperature (T = 7.9 on
-  the left, near the range of the 16-velocity set) the discrete model amplifies
-  perturbations in the rarefaction: two computations that agree to 1e-14 at 500 steps
-  separate exponentially afterwards (1e-11 at 1000, 1e-3 at 2000 steps), with the same
-  distance to the exact solution; with the temperatures divided by 10 they stay at 1e-14.
+- Lax shock tube (Sec. IV.B, workloads.lax: dx = 3e-3, dt = 1e-5, rates 2e3 / 1e3 /
+  1e5): the paper's parameters put the model in its unstable regime (s5 fifty times
+  below the rates of the higher moments; left state T = 7.9).  Round-off is amplified in
+  the rarefaction: computations that agree to 1e-14 at 500 steps separate exponentially
+  (1e-11 at 1000, 1e-3 at 2000 steps), and the oracle with the initial temperature
+  perturbed by 1e-12 goes non-finite by step 9000, so whether a run reaches the paper's
+  t = 0.45 depends on its rounding.  The GPU run is therefore compared with the exact
+  Riemann solution at t = 0.05 (5000 steps; mean absolute errors of rho, u, p below 0.01,
+  the oracle giving 0.0063, 0.0080, 0.0076) and with the oracle over the first 500 steps
+  (1e-10).
 """
 import numpy as np
 import pytest
@@ -80,15 +82,16 @@ def test_discontinuity_lax_wendroff_oscillates(lbm):
 
 def test_lax_tube_follows_exact_solution(lbm):
     p = wl.lax()
+    p.steps = 5000                                   # t = 0.05, inside the stable window
     rho, u, _, T = _gpu_rho(lbm, p)
     L, Rt = p.meta["left"], p.meta["right"]
     sol = R.solve((L[0], L[1], L[0] * L[3]), (Rt[0], Rt[1], Rt[0] * Rt[3]), 1.4)
     x = (np.arange(p.nx) + 0.5) * p.dx
     t = p.steps * p.dt
     re, ue, pe = sol.sample((x - 0.5 * p.nx * p.dx) / t)
-    assert np.abs(rho - re).mean() <= 0.02
-    assert np.abs(u - ue).mean() <= 0.02
-    assert np.abs(rho * T - pe).mean() <= 0.02
+    assert np.abs(rho - re).mean() <= 0.01
+    assert np.abs(u - ue).mean() <= 0.01
+    assert np.abs(rho * T - pe).mean() <= 0.01
     # the end cells are outside the waves (uniform inflow states, drifting only by round-off)
     assert np.abs(rho[:5] - L[0]).max() <= 1e-8 and np.abs(rho[-5:] - Rt[0]).max() <= 1e-8
 
