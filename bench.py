@@ -187,7 +187,7 @@ def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):
                                                  d="dev" if precision else "plain")
     s.init(*p.fields())
     s.step(warmup)
-    s.totals()
+    totals_start = s.totals()
     torch.cuda.synchronize(device)
     stream = torch.cuda.current_stream(device)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -231,8 +231,40 @@ def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):
     return {
         "ms": ms, "ms_local": ms_local, "step_kernel_ms": step_kernel_ms, "ghost_ms": ghost_ms,
         "launches": launches, "e2e_s": e2e_s, "e2e_rc": rc, "totals": [float(x) for x in totals_end],
-        "kernel": kernel,
+        "kernel": kernel, "totals_drift": totals_drift(totals_start, totals_end, steps),
     }
+
+
+def totals_drift(t0, t1, steps):
+    """Drift of the conserved totals (mass, momentum, energy; exactly conserved by the flux
+    form on a periodic grid) over `steps` steps, relative to the mass and energy totals."""
+    m, e = abs(float(t0[0])), abs(float(t0[3]))
+    return {"steps": steps, "mass": abs(float(t1[0]) - float(t0[0])) / m,
+            "momentum_x": abs(float(t1[1]) - float(t0[1])) / m,
+            "momentum_y": abs(float(t1[2]) - float(t0[2])) / m,
+            "energy": abs(float(t1[3]) - float(t0[3])) / e}
+
+
+def precision_compare(lbm, p, device, steps=20):
+    """FP32 deviation mode against FP64 on the same fields after `steps` steps: L1 and max
+    relative errors of rho, u (as a vector) and T over the whole grid."""
+    import numpy as np
+    out = {}
+    for prec in (lbm.LBM_FP64, lbm.LBM_FP32_DEV):
+        s = lbm.Solver.from_problem(p, precision=prec, device=device)
+        s.init(*p.fields())
+        s.step(steps)
+        out[prec] = s.moments()
+        s.close()
+    a, b = out[lbm.LBM_FP32_DEV], out[lbm.LBM_FP64]
+
+    def rel(x, y):
+        return {"l1": float(np.abs(x - y).sum() / np.abs(y).sum()), "max": float(np.abs(x - y).max() / np.abs(y).max())}
+    du = np.maximum(np.abs(a[1] - b[1]), np.abs(a[2] - b[2]))
+    umax = max(np.abs(b[1]).max(), np.abs(b[2]).max())
+    usum = (np.abs(b[1]) + np.abs(b[2])).sum()
+    return {"steps": steps, "rho": rel(a[0], b[0]), "T": rel(a[3], b[3]),
+            "u": {"l1": float(du.sum() / usum), "max": float(du.max() / umax)}}
 
 
 def cpu_baseline_run(p_full, crop: int, steps_budget_s: float = 12.0, max_steps: int = 400):
@@ -311,9 +343,12 @@ def gpu_arm(args):
         "gpu_launches": r32["launches"],
         "clocks": clocks,
         "kernel_ms": {"step": r32["step_kernel_ms"], "ghost": r32["ghost_ms"]},
+        "totals_drift": r32["totals_drift"],
     }
     if args.mode == "both":
         line["fp64"] = fp64_line(lbm, p, args, device, world, hbm)
+        if rank == 0:
+            line["precision"] = precision_compare(lbm, p, device)
     finish(line, p, args, rank, world)
 
 
@@ -342,6 +377,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
                 "h2d_bytes_per_step": 4 * 8 * cells / k64, "d2h_bytes_per_step": 4 * 8 * cells / k64},
         "gpu_launches": r64["launches"], "clocks": clk64.summary(),
         "kernel_ms": {"step": r64["step_kernel_ms"], "ghost": r64["ghost_ms"]},
+        "totals_drift": r64["totals_drift"],
     }
 
 

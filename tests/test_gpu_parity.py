@@ -196,6 +196,28 @@ def test_fp32_totals_drift(lbm):
     assert np.abs(t1[1:3] - t0[1:3]).max() <= 1e-6 * abs(t0[0])
 
 
+def test_shock_interface_full_size_100_steps(orc, lbm):
+    """The 4096 x 1024 shock-interface problem in full (every cell): 100 steps on the GPU
+    against the oracle, float64 to 1e-10 and the float32 deviation mode within its budget."""
+    p = wl.shock_interface()
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*p.fields())
+    O.step(100)
+    for prec in (0, 1):
+        s = lbm.Solver.from_problem(p, precision=prec)
+        s.init(*p.fields())
+        s.step(100)
+        if prec == 0:
+            _assert_fp64(fp64_errors(s, O))
+        else:
+            e, _ = _fp32_errors(s, O)
+            for k in ("rho_l1", "T_l1", "u_l1"):
+                assert e[k] <= 1e-4, e
+            for k in ("rho_max", "T_max", "u_max"):
+                assert e[k] <= 1e-3, e
+        s.close()
+
+
 # ------------------------------------------------------------------ full size, sampled
 def _patch(f_rows, y_local, x, nx):
     """[16][5][5] neighbourhood (periodic in x) of cell (x, y_local) from a row window."""
