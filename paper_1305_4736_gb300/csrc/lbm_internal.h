@@ -61,6 +61,7 @@ constexpr int kTmaTT = 8;
 template <typename R>
 struct TmaShape {
     static constexpr int TT = sizeof(R) == sizeof(float) ? 4 : 8;   // warps per CTA
+    static constexpr int CTAS = sizeof(R) == sizeof(float) ? (TT == 4 ? 4 : (TT == 3 ? 5 : 7)) : 1;   // per SM
     static constexpr int KR = 4;                       // rows per thread
     static constexpr int TR = TT * KR;                 // tile rows
     static constexpr int HX = 2;                       // x halo (8-byte elements: 16-byte TMA origin)

@@ -109,7 +109,7 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
 }
 
 template <typename R, bool Dev, int Lim>
-__global__ void __launch_bounds__(kTmaTX * TmaShape<R>::TT, sizeof(R) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(kTmaTX * TmaShape<R>::TT, TmaShape<R>::CTAS)
 k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, R *__restrict__ fout,
            int *err)
 {

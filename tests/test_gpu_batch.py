@@ -110,7 +110,8 @@ def test_autotune_keeps_state_and_parity(orc, lbm, prec):
     s.step(10)
     before = s.get_state()
     choice = s.autotune(3)
-    assert choice in (1, 2, 3, 4)
+    assert choice in (1, 2, 3, 4, 5, 6, 7)
+    assert s.step_kernel == choice
     assert np.array_equal(s.get_state(), before)
     assert s.step_count == 10
     s.step(90)
