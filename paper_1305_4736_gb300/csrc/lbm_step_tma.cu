@@ -140,6 +140,19 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                      " [%0], [%1, {%2, %3, %4}], [%5];"
                      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 + OX - S::HX), "r"(y0),
                      "r"(0), "r"(bar_a) : "memory");
+        if constexpr (sizeof(R) == sizeof(float)) {
+            // CTAs start in launch order: bring the tile of the CTA about half a resident wave
+            // later (CTAS x SMs / 2 blocks on) into L2, so that its copy is served from L2
+            unsigned nsm;
+            asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+            const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            const long long bn = b + (long long)S::CTAS * nsm / 2;
+            if (bn < (long long)gridDim.x * gridDim.y) {
+                const int xn = (int)(bn % gridDim.x) * kTmaTX + OX - S::HX, yn = (int)(bn / gridDim.x) * S::TR;
+                asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                             ::"l"(reinterpret_cast<unsigned long long>(&tm)), "r"(xn), "r"(yn), "r"(0) : "memory");
+            }
+        }
     }
     const bool ok = mbar_wait(bar_a, 0);
     if (!__syncthreads_and(ok)) {
