@@ -133,8 +133,9 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
                   const lbm_options *opt, lbm_ctx **out);
 
 /* Initialise every interior cell to f = M^-1 f_hat^eq(rho, u, v, T) (Appendix A;
-   the initialisation practice of Sec. IV.A).  Host arrays [ny][nx]; rho > 0, T > 0
-   (LBM_ERR_ARG otherwise).  Synchronous. */
+   the initialisation practice of Sec. IV.A).  Host arrays [ny][nx] (pinned memory lets the
+   copies run asynchronously); rho > 0, T > 0 and finite values, checked on the device:
+   LBM_ERR_ARG otherwise, and the context is then left uninitialised.  Synchronous. */
 int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *v, const double *T);
 
 /* Enqueue n >= 1 time steps (ghost fill + fused collide/convect per step; Eq. (3) and

@@ -41,6 +41,7 @@ struct lbm_ctx {
     size_t aux_bytes = 0;
     int *flag = nullptr;          // non-finite / rho <= 0 seen by the moments kernel
     int *tma_err = nullptr;       // a copy wait ran out in a TMA-fed step kernel
+    int *init_err = nullptr;      // an lbm_init field value was invalid
     double *tot_out = nullptr;
     bool use_tma = false;
     bool use_stream = false;
@@ -470,6 +471,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->tot_out = c->aux + lbm::kTotalsBlocks * NQ;
     c->flag = (int *)(c->tot_out + 4);
     c->tma_err = c->flag + 1;
+    c->init_err = c->flag + 2;
     int want = opt ? opt->step_kernel : 0;
     if (want < 0 || want > 7) {
         lbm_destroy(c);
@@ -535,14 +537,16 @@ int lbm_init(lbm_ctx *c, const double *rho, const double *u, const double *v, co
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (!rho || !u || !v || !T) return fail(c, LBM_ERR_ARG, "NULL field");
-    const long long n = (long long)c->P.nx * c->P.ny;
-    for (long long i = 0; i < n; i++)
-        if (!finite_pos(rho[i]) || !finite_pos(T[i]) || !std::isfinite(u[i]) || !std::isfinite(v[i]))
-            return fail(c, LBM_ERR_ARG, "init fields need rho > 0, T > 0 and finite values");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    // the fields are checked by the init kernel (rho > 0, T > 0, finite), which flags a bad cell
+    c->initialized = false;
+    ce = cudaMemsetAsync(c->init_err, 0, sizeof(int), c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "flag reset");
     const int R = rows_per_chunk(c, 4);
     const int nx = c->P.nx;
+    // one stream: each chunk's copies follow the previous chunk's kernel, so the staging
+    // buffer is reused without waiting on the host
     for (int r0 = 0; r0 < c->P.ny; r0 += R) {
         const int rows = std::min(R, c->P.ny - r0);
         const size_t m = (size_t)rows * nx;
@@ -552,11 +556,14 @@ int lbm_init(lbm_ctx *c, const double *rho, const double *u, const double *v, co
                                  cudaMemcpyHostToDevice, c->stream);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "init copy");
         }
-        ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], c->stage, r0, rows, c->stream);
+        ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], c->stage, r0, rows, c->init_err, c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "init kernel");
-        ce = cudaStreamSynchronize(c->stream);   // the staging buffer is reused by the next chunk
-        if (ce != cudaSuccess) return cuda_fail(c, ce, "init");
     }
+    int bad = 0;
+    ce = cudaMemcpyAsync(&bad, c->init_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "init");
+    if (bad) return fail(c, LBM_ERR_ARG, "init fields need rho > 0, T > 0 and finite values");
     c->initialized = true;
     c->steps = 0;
     return LBM_OK;
@@ -619,12 +626,12 @@ static int moments_impl(lbm_ctx *c, double *rho, double *u, double *v, double *T
                 if (ce != cudaSuccess) return cuda_fail(c, ce, "moments copy");
             }
         }
-        ce = cudaStreamSynchronize(c->stream);
-        if (ce != cudaSuccess) return cuda_fail(c, ce, "moments");
+        // the next chunk's kernel follows these copies on the stream: no host wait here
     }
     int flags[2] = {0, 0};
-    ce = cudaMemcpy(flags, c->flag, sizeof(flags), cudaMemcpyDeviceToHost);
-    if (ce != cudaSuccess) return cuda_fail(c, ce, "flag copy");
+    ce = cudaMemcpyAsync(flags, c->flag, sizeof(flags), cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "moments");
     if (flags[1]) return fail(c, LBM_ERR_TIMEOUT, "a copy wait ran out in the step kernel");
     if (flags[0]) return fail(c, LBM_ERR_NONFINITE, "a cell has a non-finite value or rho <= 0");
     return LBM_OK;
@@ -677,9 +684,9 @@ int lbm_get_state(lbm_ctx *c, double *f)
                                  cudaMemcpyDeviceToHost, c->stream);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "state copy");
         }
-        ce = cudaStreamSynchronize(c->stream);
-        if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state");
     }
+    ce = cudaStreamSynchronize(c->stream);   // chunks are ordered on the stream; one wait at the end
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state");
     return LBM_OK;
 }
 
@@ -703,9 +710,9 @@ int lbm_get_state_rows(lbm_ctx *c, int row0, int rows, double *f)
                                  cudaMemcpyDeviceToHost, c->stream);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "state copy");
         }
-        ce = cudaStreamSynchronize(c->stream);
-        if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state_rows");
     }
+    ce = cudaStreamSynchronize(c->stream);   // chunks are ordered on the stream; one wait at the end
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "get_state_rows");
     return LBM_OK;
 }
 
@@ -727,9 +734,9 @@ int lbm_set_state(lbm_ctx *c, const double *f)
         }
         ce = lbm::launch_unpack(c->P, c->prec, c->f[c->cur], r0, rows, c->stage, c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "unpack kernel");
-        ce = cudaStreamSynchronize(c->stream);
-        if (ce != cudaSuccess) return cuda_fail(c, ce, "set_state");
     }
+    ce = cudaStreamSynchronize(c->stream);   // chunks are ordered on the stream; one wait at the end
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "set_state");
     c->initialized = true;
     c->steps = 0;
     return LBM_OK;

@@ -16,7 +16,7 @@ constexpr int kTotalsThreads = 256;
 
 // All launchers enqueue on `st` and return the launch status.
 // `prec` is the storage precision (0 = float64 f, 1 = float32 deviation g).
-cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows,
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows, int *bad,
                         cudaStream_t st);
 cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
 // Plain fused step with tiles of 32 x ty cells (ty = 4, 8 or 16).

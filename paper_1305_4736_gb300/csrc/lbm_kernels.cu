@@ -308,9 +308,10 @@ __global__ void k_ghost_batch(const Params *__restrict__ Pall, const BatchGrid *
 // Initialisation from macroscopic fields (float64 arithmetic in both modes).
 // fields = [4][rows][nx] (rho, u, v, T) for interior rows row0 .. row0+rows-1.
 // ---------------------------------------------------------------------------
+// A cell with rho <= 0, T <= 0 or a non-finite value sets *bad and is not written.
 template <typename R, bool Dev>
 __global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, const double *__restrict__ fields,
-                       int row0, int rows)
+                       int row0, int rows, int *bad)
 {
     const int nx = P.nx;
     const long long n = (long long)rows * nx;
@@ -318,6 +319,10 @@ __global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, cons
     if (i >= n) return;
     const int x = (int)(i % nx), y = row0 + (int)(i / nx);
     const double rho = fields[i], ux = fields[n + i], uy = fields[2 * n + i], T = fields[3 * n + i];
+    if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(uy)) {
+        atomicOr(bad, 1);
+        return;
+    }
     const Coef<double> &C = P.cd;
     const double drho = rho - C.rho0;
     const double dP = rho * T - C.P0;
@@ -552,13 +557,13 @@ __global__ void k_unpack(const __grid_constant__ Params P, R *__restrict__ f, in
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows,
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows, int *bad,
                         cudaStream_t st)
 {
     const long long n = (long long)rows * P.nx;
     if (n == 0) return cudaSuccess;
-    if (prec == 0) k_init<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, fields, row0, rows);
-    else k_init<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, fields, row0, rows);
+    if (prec == 0) k_init<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, fields, row0, rows, bad);
+    else k_init<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, fields, row0, rows, bad);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,27 @@ def test_step_before_init_and_bad_n(lbm):
     assert e.value.code == lbm.LBM_ERR_STATE
 
 
+@pytest.mark.parametrize("field,value", [(0, 0.0), (0, -1.0), (1, float("nan")), (3, 0.0), (2, float("inf"))])
+def test_invalid_init_fields_are_rejected_on_the_device(lbm, field, value):
+    """lbm_init checks rho > 0, T > 0 and finiteness in the init kernel: one bad cell (in the
+    second of several staging chunks) gives LBM_ERR_ARG and leaves the context uninitialised;
+    a valid init afterwards works."""
+    p = wl.shear_layer(1600, ny=1500)                    # 2.4 M cells: two staging chunks
+    bad = [np.array(a, copy=True) for a in p.fields()]
+    bad[field][1400, 777] = value
+    s = lbm.Solver.from_problem(p, precision=1)
+    with pytest.raises(lbm.LbmError) as e:
+        s.init(*bad)
+    assert e.value.code == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(1)
+    assert e.value.code == lbm.LBM_ERR_STATE
+    s.init(*p.fields())
+    s.step(2)
+    assert np.isfinite(s.moments()[0]).all()
+    s.close()
+
+
 def test_nonfinite_state_is_reported(lbm):
     p = wl.sod(200, 2)
     s = lbm.Solver.from_problem(p)
