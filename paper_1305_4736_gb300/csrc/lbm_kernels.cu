@@ -253,8 +253,14 @@ __device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, i
     const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
     if (E.kind == 0 || E.kind == 1) {                       // periodic / zero gradient
         const long long cs = (long long)(sy + OY) * P.pitch + (sx + OX);
+        if constexpr (sizeof(R) == sizeof(float)) {             // pair planes: one 8-byte copy per pair
+            float2 *f2p = reinterpret_cast<float2 *>(f);
 #pragma unroll
-        for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = f[pidx<R>(q, plane, cs)];
+            for (int pr = 0; pr < 8; pr++) f2p[pr * plane + cg] = f2p[pr * plane + cs];
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = f[pidx<R>(q, plane, cs)];
+        }
     } else if (E.kind == 2) {                               // fixed equilibrium
 #pragma unroll
         for (int q = 0; q < NQ; q++) f[pidx<R>(q, plane, cg)] = pick<R>(E.feq[q], E.feqf[q]);

@@ -155,3 +155,32 @@ def test_pipe_is_float32_only(lbm):
     p = wl.shock_interface(nx=150, ny=70, steps=1)
     with pytest.raises(lbm.LbmError):
         lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter, p.bc, precision=0, step_kernel=6)
+
+
+# ------------------------------------------------ TMA-staged kernel across state changes
+def test_tma_kernel_across_set_state_and_batch_steps(lbm):
+    """The float32 TMA-staged kernel on a ragged doubly periodic grid, stepped in uneven chunks
+    with a get_state / set_state round trip and a batch step in between, matches the plain
+    kernel to round-off."""
+    p = _crop(wl.shear_layer(160, seed=8, steps=60), 150, 70)     # ragged against 32 x 16 tiles
+    ref = lbm.Solver.from_problem(p, precision=1, step_kernel=1)
+    ref.init(*p.fields())
+    s = lbm.Solver.from_problem(p, precision=1, step_kernel=2)
+    s.init(*p.fields())
+    for chunk in (7, 13, 1):
+        ref.step(chunk)
+        s.step(chunk)
+    mid = s.get_state()
+    s.set_state(mid)
+    ref.set_state(ref.get_state())
+    b = lbm.Batch([s])
+    b.step(3)
+    b.close()
+    ref.step(3)
+    s.step(36)
+    ref.step(36)
+    got, want = s.get_state(), ref.get_state()
+    s.close()
+    ref.close()
+    assert np.isfinite(got).all()
+    assert np.abs(got - want).max() <= ROUNDOFF[1] * np.abs(want).max()
