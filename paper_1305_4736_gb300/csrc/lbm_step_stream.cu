@@ -128,6 +128,29 @@ template <typename R> struct Win;
 template <> struct Win<float> { float2 w[8], d[8], m[8]; };
 template <> struct Win<double> { double w[NQ], d[NQ], m[NQ]; };
 
+// float64: the shells and conserved moments of a row, computed for its flow velocity one step
+// before its collision, are carried to that collision (the float64 pipe bounds that kernel).
+struct Carry64 {
+    Shells<double> sh;
+    double drho, jx, jy, de;
+};
+
+template <bool Dev>
+__device__ __forceinline__ void moments_at(const Coef<double> &C, const double *p, Carry64 &c, double &u, double &v,
+                                           double &ir)
+{
+    constexpr int BW = StreamShape<double>::BW;
+    double g[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) g[q] = p[q * BW];
+    c.sh = shells_of(g);
+    conserved_of(c.sh, c.drho, c.jx, c.jy, c.de);
+    const double rho = Dev ? C.rho0 + c.drho : c.drho;
+    ir = recip(rho);
+    u = c.jx * ir;
+    v = c.jy * ir;
+}
+
 // Window at the first row y0 of a segment from rows y0-2 (a), y0-1 (b), y0 (c), y0+1 (d).
 // sy > 0: oriented slope at index c is slope2(D[c-1], D[c]) (D[m] = w[m+1] - w[m]); carry
 //         w(y0), D between y0-1 and y0, slope at y0-1.
@@ -364,7 +387,11 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
         if (!ok) break;
         R u_m, v_m, u_0, v_0, ir_0, dummy;
         flow_at<Dev>(C, colp(row_at(pb)), BW, u_m, v_m, dummy);
-        flow_at<Dev>(C, colp(row_at(pc)), BW, u_0, v_0, ir_0);
+        [[maybe_unused]] Carry64 c0;      // float64: moments of row y, carried from phase 1
+        if constexpr (sizeof(R) == sizeof(float))
+            flow_at<Dev>(C, colp(row_at(pc)), BW, u_0, v_0, ir_0);
+        else
+            moments_at<Dev>(C, colp(row_at(pc)), c0, u_0, v_0, ir_0);
         Win<R> W;
         win_init<Lim>(W, colp(row_at(pa)), colp(row_at(pb)), colp(row_at(pc)), colp(row_at(pd)));
         release(kb, pa.slot);
@@ -376,7 +403,11 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
             if (!(ok = wait(p2))) break;
             const R *r0 = row_at(p0), *r1 = row_at(p1), *r2 = row_at(p2);
             R u_p, v_p, ir_p;
-            flow_at<Dev>(C, colp(r1), BW, u_p, v_p, ir_p);
+            [[maybe_unused]] Carry64 c1;
+            if constexpr (sizeof(R) == sizeof(float))
+                flow_at<Dev>(C, colp(r1), BW, u_p, v_p, ir_p);
+            else
+                moments_at<Dev>(C, colp(r1), c1, u_p, v_p, ir_p);
             R uh, vh;
             halo_velocity<R, Dev>(C, r0 + hoff, cxl, cyl, uh, vh);
             R uxm = __shfl_up_sync(0xffffffffu, u_0, 1), uxp = __shfl_down_sync(0xffffffffu, u_0, 1);
@@ -401,13 +432,11 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
                 double f[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; q++) f[q] = s0[q * BW];
-                const Shells<double> sh = shells_of(f);
-                double drho, jx, jy, de;
-                conserved_of(sh, drho, jx, jy, de);
                 double acc[NQ];
-                collide<double, Dev>(P, sh, drho, jx, jy, de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm, v_p - v_m,
-                                     acc);
+                collide<double, Dev>(P, c0.sh, c0.drho, c0.jx, c0.jy, c0.de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm,
+                                     v_p - v_m, acc);
                 convect_store<Lim>(C, W, f, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg);
+                c0 = c1;
             }
             u_m = u_0;
             u_0 = u_p;
