@@ -321,9 +321,21 @@ __device__ __forceinline__ float mc2(float a, float b)
     return r;
 }
 
-// 1/x: correctly rounded in float64; in float32 the hardware reciprocal
+// 1/x.  float64: Newton-Raphson iteration for the reciprocal, y <- y + y (1 - x y), which
+// squares the relative error at each step, from the approximate reciprocal of PTX
+// (rcp.approx.ftz.f64, about 20 correct bits); two steps reach the rounding level (within an
+// ulp or so of the correctly rounded quotient) in five float64 operations, fewer than an IEEE
+// division.  x is a density, positive and normal.  float32: the hardware reciprocal
 // approximation (at most 2 ulp), ample for the float32 deviation mode.
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ double recip(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
 template <typename R, int Lim>
