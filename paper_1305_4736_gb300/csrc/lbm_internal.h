@@ -11,7 +11,7 @@ namespace lbm {
 constexpr int kTX = 32;
 constexpr int kTY = 8;
 // Fixed grid of the first totals pass (the result is deterministic for a given size).
-constexpr int kTotalsBlocks = 512;
+constexpr int kTotalsBlocks = 1024;   // partials buffer: at least one wave of totals blocks
 constexpr int kTotalsThreads = 256;
 
 // All launchers enqueue on `st` and return the launch status.

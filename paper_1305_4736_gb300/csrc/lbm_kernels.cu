@@ -672,15 +672,33 @@ cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, i
     return cudaGetLastError();
 }
 
+// Blocks of the totals reduction: one wave of resident blocks (the SM count x blocks per SM at
+// the kernel's register use), at most kTotalsBlocks (the partials buffer).  A second, mostly
+// empty wave would double the time of the row-strided reduction.
+static int totals_blocks(const void *fn)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTotalsThreads, 0);
+    long long n = (long long)(sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
+    if (n > kTotalsBlocks) n = kTotalsBlocks;
+    return (int)n;
+}
+
 cudaError_t launch_totals(const Params &P, int prec, const void *f, double *partial, double *out, double scale,
                           cudaStream_t st)
 {
     if (prec == 0) {
-        k_totals_partial<double, false><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const double *)f, partial);
-        k_totals_final<false><<<1, 256, 0, st>>>(P, partial, kTotalsBlocks, scale, out);
+        static const int nb = totals_blocks((const void *)k_totals_partial<double, false>);
+        const int g = nb < P.ny ? nb : (P.ny < 1 ? 1 : P.ny);
+        k_totals_partial<double, false><<<g, kTotalsThreads, 0, st>>>(P, (const double *)f, partial);
+        k_totals_final<false><<<1, 256, 0, st>>>(P, partial, g, scale, out);
     } else {
-        k_totals_partial<float, true><<<kTotalsBlocks, kTotalsThreads, 0, st>>>(P, (const float *)f, partial);
-        k_totals_final<true><<<1, 256, 0, st>>>(P, partial, kTotalsBlocks, scale, out);
+        static const int nb = totals_blocks((const void *)k_totals_partial<float, true>);
+        const int g = nb < P.ny ? nb : (P.ny < 1 ? 1 : P.ny);
+        k_totals_partial<float, true><<<g, kTotalsThreads, 0, st>>>(P, (const float *)f, partial);
+        k_totals_final<true><<<1, 256, 0, st>>>(P, partial, g, scale, out);
     }
     return cudaGetLastError();
 }
