@@ -296,16 +296,35 @@ __host__ __device__ __forceinline__ void pop_from_moments(const Coef<R> &C, cons
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double mc2(double a, double b)
 {
-    // 2 * minmod(2a, (a+b)/2, 2b) = sign * min(4|a|, 4|b|, |a+b|)
-    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-    const long long mask = 0x7fffffffffffffffLL;
-    const long long aa = ia & mask, ab = ib & mask;
-    const long long m = aa < ab ? aa : ab;
-    const long long im4 = m + (2LL << 52);                 // 4 |m| (exponent + 2)
-    const long long id = __double_as_longlong(a + b) & mask;
-    const long long r = im4 < id ? im4 : id;
-    const bool same = ((ia ^ ib) >= 0) && (m != 0);
-    return __longlong_as_double(same ? (r | (ib & ~mask)) : 0LL);
+    // 2 * minmod(2a, (a+b)/2, 2b) = sign * min(4|a|, 4|b|, |a+b|).  The integer steps are
+    // written in PTX: as C++ bit operations the compiler recognises the sign-bit masks as
+    // fabs and evaluates them as float64 instructions.
+    const double s = a + b;
+    double r;
+    asm("{\n\t"
+        ".reg .b64 ia, ib, is, aa, ab, m, t, sg;\n\t"
+        ".reg .pred pd, pz;\n\t"
+        "mov.b64 ia, %1;\n\t"
+        "mov.b64 ib, %2;\n\t"
+        "mov.b64 is, %3;\n\t"
+        "and.b64 aa, ia, 0x7FFFFFFFFFFFFFFF;\n\t"
+        "and.b64 ab, ib, 0x7FFFFFFFFFFFFFFF;\n\t"
+        "min.u64 m, aa, ab;\n\t"                      // min(|a|, |b|)
+        "setp.eq.u64 pz, m, 0;\n\t"
+        "add.u64 m, m, 0x0020000000000000;\n\t"       // 4 min(|a|, |b|): exponent + 2
+        "and.b64 is, is, 0x7FFFFFFFFFFFFFFF;\n\t"
+        "min.u64 t, m, is;\n\t"
+        "xor.b64 sg, ia, ib;\n\t"
+        "setp.lt.s64 pd, sg, 0;\n\t"                  // the differences disagree in sign
+        "or.pred pd, pd, pz;\n\t"
+        "and.b64 sg, ib, 0x8000000000000000;\n\t"
+        "or.b64 t, t, sg;\n\t"
+        "selp.b64 t, 0, t, pd;\n\t"
+        "mov.b64 %0, t;\n\t"
+        "}"
+        : "=d"(r)
+        : "d"(a), "d"(b), "d"(s));
+    return r;
 }
 
 __device__ __forceinline__ float mc2(float a, float b)
@@ -365,8 +384,9 @@ __device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R 
     R q[NQ];
     feq_hat_dev<R, Dev>(C, drho, jx, jy, dP, ir, q);
     R D[NQ];
+    D[4] = (de - R(kEta2) * sh.S[0]) - q[4];   // row 5 from the caller's e (equal to M.m[3])
 #pragma unroll
-    for (int k = 4; k < NQ; k++) D[k] = M.m[k] - q[k];
+    for (int k = 5; k < NQ; k++) D[k] = M.m[k] - q[k];
     if (P.has_c9) {
         const R Pt = Dev ? C.P0 + dP : dP;
         // y differences weighted by ry = dx/dy (q8, q9 carry 1/(2 dx))

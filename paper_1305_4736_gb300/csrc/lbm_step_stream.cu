@@ -200,7 +200,7 @@ __device__ __forceinline__ void win_init(Win<double> &W, const double *a, const 
             const double d1 = c[o] - b[o], d2 = d[o] - c[o];
             W.w[q] = d[o];
             W.d[q] = d2;
-            W.m[q] = slope2<double, Lim>(-d2, -d1);
+            W.m[q] = slope2<double, Lim>(d2, d1);   // the oriented slope, negated (slope2 is odd)
         }
     }
 }
@@ -274,8 +274,10 @@ __device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double>
                 tyv = Lim == 2 ? W.d[q] : W.d[q] + hy * (mn - W.m[q]);
                 W.m[q] = mn;
             } else {
-                const double mn = slope2<double, Lim>(-dn, -W.d[q]);
-                tyv = Lim == 2 ? -W.d[q] : -W.d[q] + hy * (W.m[q] - mn);
+                // negated oriented slopes and flux: slope2 is odd, and float64 negations would
+                // take float64 instructions
+                const double mn = slope2<double, Lim>(dn, W.d[q]);
+                tyv = Lim == 2 ? W.d[q] : W.d[q] + hy * (W.m[q] - mn);
                 W.m[q] = mn;
             }
             W.w[q] = wn;
@@ -283,7 +285,8 @@ __device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double>
         }
         // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
         double out = f[q] - acc[q];
-        if (sy != 0) out -= C.cry[shell] * tyv;
+        if (sy > 0) out -= C.cry[shell] * tyv;
+        if (sy < 0) out += C.cry[shell] * tyv;
         if (sx != 0) out -= C.cr[shell] * tx;
         if (store) fout[q * plane + cg] = out;
     }

@@ -214,12 +214,13 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                 yd[q] = d1;
                 ym[q] = slope2<R, Lim>(d0, d1);
             } else {
-                // oriented slope at index c: slope2(-D[c], -D[c-1]); carry w[3], D[2], slope at index 2
+                // oriented slope at index c: slope2(-D[c], -D[c-1]); carry w[3], D[2] and the slope
+                // at index 2 negated, slope2(D[2], D[1]) (slope2 is odd; no negations in float64)
                 const R w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
                 const R d1 = w2 - w1, d2 = w3 - w2;
                 yw[q] = w3;
                 yd[q] = d2;
-                ym[q] = slope2<R, Lim>(-d2, -d1);
+                ym[q] = slope2<R, Lim>(d2, d1);
             }
         }
 
@@ -268,9 +269,10 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                         tyv = Lim == 2 ? yd[q] : yd[q] + hy * (mn - ym[q]);
                         ym[q] = mn;
                     } else {
-                        // D[k+3], slope at J - sigma = index k+3; flux -D[k+2] + h (slope_J - slope_{J+1})
-                        const R mn = slope2<R, Lim>(-dn, -yd[q]);
-                        tyv = Lim == 2 ? -yd[q] : -yd[q] + hy * (ym[q] - mn);
+                        // D[k+3], slope at J - sigma = index k+3; flux -D[k+2] + h (slope_J - slope_{J+1}),
+                        // carried negated: tyv = D[k+2] + h (-slope_J + slope_{J+1})
+                        const R mn = slope2<R, Lim>(dn, yd[q]);
+                        tyv = Lim == 2 ? yd[q] : yd[q] + hy * (ym[q] - mn);
                         ym[q] = mn;
                     }
                     yw[q] = wn;
@@ -278,7 +280,8 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
                 }
                 // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
                 R out = f[q] - acc[q];
-                if (sy != 0) out -= C.cry[shell] * tyv;
+                if (sy > 0) out -= C.cry[shell] * tyv;
+                if (sy < 0) out += C.cry[shell] * tyv;
                 if (sx != 0) out -= C.cr[shell] * tx;
                 if (store) fout[q * P.plane + cg] = out;
             }
