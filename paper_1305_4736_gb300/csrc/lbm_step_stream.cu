@@ -151,6 +151,50 @@ __device__ __forceinline__ void moments_at(const Coef<double> &C, const double *
     v = c.jy * ir;
 }
 
+// float64 MC x convection shared between lanes.  For an x-moving population with sign s,
+// D(x) = f(x) - f(x-s) and the slope Sl(x) = mc2(D(x), D(x+s)); the flux difference at x is
+// D(x) + h (Sl(x) - Sl(x-s)).  Each lane forms D and Sl at its own column once and takes
+// D(x+s) and Sl(x-s) from its neighbours by shuffles.  The two lanes at the warp's edges
+// need values one column outside the warp: per row, lanes 0..11 form D beyond the downwind
+// edge of x-stencil k = lane, and lanes 12..23 the slope before the upwind edge of
+// stencil k = lane - 12, in three float64 instructions for all twelve stencils.
+__host__ __device__ __forceinline__ constexpr int xstencil_q(int k) { return k < 4 ? 2 * k : k + 4; }
+__host__ __device__ __forceinline__ constexpr int xstencil_of(int q) { return q < 8 ? q >> 1 : q - 4; }
+
+struct XEdge {
+    int o0, o1, o2;   // this lane's three row offsets (plane * BW + column)
+    double t1, E;     // lanes 0..11: D beyond the downwind edge; lanes 12..23: D(xu), Sl(xu - s)
+};
+
+// Offsets of the edge values for this lane; wcol: column of the warp's first cell in its
+// half row (the warp's columns are wcol .. wcol + 31).
+__device__ __forceinline__ void xedge_setup(XEdge &e, int lane, int wcol)
+{
+    constexpr int BW = StreamShape<double>::BW;
+    const bool down = lane < 12;
+    const int k = down ? lane : (lane - 12 < 11 ? lane - 12 : 11);
+    const int q = xstencil_q(k), sx = tsgn_x(q);
+    const int base = q * BW + wcol;
+    if (down) {
+        const int xd = sx > 0 ? 31 : 0;              // downwind edge lane's column
+        e.o0 = base + xd;
+        e.o1 = base + xd;
+        e.o2 = base + xd + sx;                       // D(xd + s) = f(xd + s) - f(xd)
+    } else {
+        const int xu = sx > 0 ? 0 : 31;              // upwind edge lane's column
+        e.o0 = base + xu - 2 * sx;
+        e.o1 = base + xu - sx;
+        e.o2 = base + xu;                            // Sl(xu - s) = mc2(D(xu - s), D(xu))
+    }
+}
+
+__device__ __forceinline__ void xedge_row(XEdge &e, const double *row)
+{
+    const double p0 = row[e.o0], p1 = row[e.o1], p2 = row[e.o2];
+    e.t1 = p2 - p1;
+    e.E = mc2(p1 - p0, e.t1);
+}
+
 // Window at the first row y0 of a segment from rows y0-2 (a), y0-1 (b), y0 (c), y0+1 (d).
 // sy > 0: oriented slope at index c is slope2(D[c-1], D[c]) (D[m] = w[m+1] - w[m]); carry
 //         w(y0), D between y0-1 and y0, slope at y0-1.
@@ -255,9 +299,10 @@ template <int Lim>
 __device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double> &W, const double *f,
                                               const double *acc, const double *s0, const double *s1,
                                               const double *s2, bool store, double *__restrict__ fout,
-                                              long long plane, long long cg)
+                                              long long plane, long long cg, const XEdge &xe, int lane)
 {
     constexpr int BW = StreamShape<double>::BW;
+    constexpr unsigned kAll = 0xffffffffu;
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
         const int sx = tsgn_x(q), sy = tsgn_y(q);
@@ -265,7 +310,20 @@ __device__ __forceinline__ void convect_store(const Coef<double> &C, Win<double>
         const int o = q * BW;
         const double hy = C.hhy[shell];
         double tx = 0.0, tyv = 0.0;
-        if (sx != 0) tx = flux_diff<double, Lim>(s0[o - 2 * sx], s0[o - sx], f[q], s0[o + sx], C.hh[shell]);
+        if (sx != 0 && Lim == 0) {
+            const int k = xstencil_of(q);
+            const double D = f[q] - s0[o - sx];
+            double Dn = sx > 0 ? __shfl_down_sync(kAll, D, 1) : __shfl_up_sync(kAll, D, 1);
+            const double De = __shfl_sync(kAll, xe.t1, k);
+            if (lane == (sx > 0 ? 31 : 0)) Dn = De;
+            const double Sl = mc2(D, Dn);
+            double Sp = sx > 0 ? __shfl_up_sync(kAll, Sl, 1) : __shfl_down_sync(kAll, Sl, 1);
+            const double Se = __shfl_sync(kAll, xe.E, 12 + k);
+            if (lane == (sx > 0 ? 0 : 31)) Sp = Se;
+            tx = D + C.hh[shell] * (Sl - Sp);
+        } else if (sx != 0) {
+            tx = flux_diff<double, Lim>(s0[o - 2 * sx], s0[o - sx], f[q], s0[o + sx], C.hh[shell]);
+        }
         if (sy != 0) {
             const double wn = (sy > 0 ? s1 : s2)[o];
             const double dn = wn - W.w[q];
@@ -351,6 +409,8 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
     using V = std::conditional_t<sizeof(R) == sizeof(float), float2, double>;
     auto colp = [&](const R *row) { return reinterpret_cast<const V *>(row) + col; };
     const int hoff = sizeof(R) == sizeof(float) ? (pair_of(hq) * BW + hcol) * 2 + member_of(hq) : hq * BW + hcol;
+    [[maybe_unused]] XEdge xe{};
+    if constexpr (sizeof(R) == sizeof(double)) xedge_setup(xe, lane, 32 * wl + 4);
     auto wait = [&](const Pos &p) {
         const bool ok = mbar_wait_or_abort(bar_a + 8u * (unsigned)p.slot, p.phase, &abort_flag);
         if (!ok && lane == 0) *(volatile int *)&abort_flag = 1;
@@ -438,7 +498,8 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
                 double acc[NQ];
                 collide<double, Dev>(P, c0.sh, c0.drho, c0.jx, c0.jy, c0.de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm,
                                      v_p - v_m, acc);
-                convect_store<Lim>(C, W, f, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg);
+                if (Lim == 0) xedge_row(xe, r0);
+                convect_store<Lim>(C, W, f, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg, xe, lane);
                 c0 = c1;
             }
             u_m = u_0;
