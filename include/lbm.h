@@ -133,9 +133,12 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
                   const lbm_options *opt, lbm_ctx **out);
 
 /* Initialise every interior cell to f = M^-1 f_hat^eq(rho, u, v, T) (Appendix A;
-   the initialisation practice of Sec. IV.A).  Host arrays [ny][nx] (pinned memory lets the
-   copies run asynchronously); rho > 0, T > 0 and finite values, checked on the device:
-   LBM_ERR_ARG otherwise, and the context is then left uninitialised.  Synchronous. */
+   the initialisation practice of Sec. IV.A).  Host arrays [ny][nx], caller-owned, not retained.
+   When all four lie in page-locked memory allocated or registered through CUDA, the init
+   kernel reads them over the host link directly; other host memory is copied through a device
+   staging buffer in chunks.  LBM_FP32_DEV evaluates the deviation g = f^eq - f^eq0 in float32
+   from float64 deviations of rho, j and P.  rho > 0, T > 0 and finite values, checked on the
+   device: LBM_ERR_ARG otherwise, and the context is then left uninitialised.  Synchronous. */
 int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *v, const double *T);
 
 /* Enqueue n >= 1 time steps (ghost fill + fused collide/convect per step; Eq. (3) and
@@ -145,8 +148,10 @@ int lbm_step(lbm_ctx *ctx, int n);
 
 /* Macroscopic fields and non-equilibrium moments Delta_k = (M f)_k - f_hat^eq_k
    (Sec. V).  Outputs [ny][nx] (rho, u, v, T) and [16][ny][nx] (delta); any output
-   may be NULL.  Synchronous.  LBM_ERR_NONFINITE if a cell has a non-finite value or
-   rho <= 0 (outputs are still written). */
+   may be NULL.  When every requested output lies in page-locked memory allocated or
+   registered through CUDA, the moments kernel writes them over the host link directly;
+   otherwise they come through a device staging buffer.  Synchronous.  LBM_ERR_NONFINITE if
+   a cell has a non-finite value or rho <= 0 (outputs are still written). */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, double *T, double *delta);
 
 /* Central non-equilibrium moments Delta*_k = (M* (f - f^eq))_k with M* built at each

@@ -524,6 +524,28 @@ int lbm_create(int nx, int ny, double dx, double dt, double gamma, double Pr, co
     return lbm_create_ex(nx, ny, dx, dt, gamma, Pr, s, limiter, bc, nullptr, out);
 }
 
+// Device address of a host array of `bytes` bytes that kernels can access directly: page-locked
+// memory allocated or registered through CUDA (cudaHostAlloc, cudaHostRegister, a pinned torch
+// tensor), checked at both ends of the range.  nullptr for any other memory.
+static void *mapped_host(const void *p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = static_cast<const char *>(p) + (bytes - 1);
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost || static_cast<char *>(b.devicePointer) != static_cast<char *>(a.devicePointer) + (bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 static int rows_per_chunk(const lbm_ctx *c, int planes)
 {
     const size_t per_row = (size_t)planes * c->P.nx;
@@ -543,21 +565,36 @@ int lbm_init(lbm_ctx *c, const double *rho, const double *u, const double *v, co
     c->initialized = false;
     ce = cudaMemsetAsync(c->init_err, 0, sizeof(int), c->stream);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "flag reset");
-    const int R = rows_per_chunk(c, 4);
-    const int nx = c->P.nx;
-    // one stream: each chunk's copies follow the previous chunk's kernel, so the staging
-    // buffer is reused without waiting on the host
-    for (int r0 = 0; r0 < c->P.ny; r0 += R) {
-        const int rows = std::min(R, c->P.ny - r0);
-        const size_t m = (size_t)rows * nx;
-        const double *src[4] = {rho, u, v, T};
-        for (int k = 0; k < 4; k++) {
-            ce = cudaMemcpyAsync(c->stage + k * m, src[k] + (size_t)r0 * nx, m * sizeof(double),
-                                 cudaMemcpyHostToDevice, c->stream);
-            if (ce != cudaSuccess) return cuda_fail(c, ce, "init copy");
-        }
-        ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], c->stage, r0, rows, c->init_err, c->stream);
+    const int nx = c->P.nx, ny = c->P.ny;
+    const size_t field_bytes = (size_t)nx * ny * sizeof(double);
+    const double *src[4] = {rho, u, v, T};
+    const double *dev[4];
+    bool direct = true;
+    for (int k = 0; k < 4; k++) {
+        dev[k] = static_cast<const double *>(mapped_host(src[k], field_bytes));
+        direct = direct && dev[k];
+    }
+    if (direct) {
+        // page-locked host fields: the init kernel reads them over the host link itself
+        ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], dev[0], dev[1], dev[2], dev[3], 0, ny, c->init_err,
+                              c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "init kernel");
+    } else {
+        const int R = rows_per_chunk(c, 4);
+        // one stream: each chunk's copies follow the previous chunk's kernel, so the staging
+        // buffer is reused without waiting on the host
+        for (int r0 = 0; r0 < ny; r0 += R) {
+            const int rows = std::min(R, ny - r0);
+            const size_t m = (size_t)rows * nx;
+            for (int k = 0; k < 4; k++) {
+                ce = cudaMemcpyAsync(c->stage + k * m, src[k] + (size_t)r0 * nx, m * sizeof(double),
+                                     cudaMemcpyHostToDevice, c->stream);
+                if (ce != cudaSuccess) return cuda_fail(c, ce, "init copy");
+            }
+            ce = lbm::launch_init(c->P, c->prec, c->f[c->cur], c->stage, c->stage + m, c->stage + 2 * m,
+                                  c->stage + 3 * m, r0, rows, c->init_err, c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "init kernel");
+        }
     }
     int bad = 0;
     ce = cudaMemcpyAsync(&bad, c->init_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -602,8 +639,23 @@ static int moments_impl(lbm_ctx *c, double *rho, double *u, double *v, double *T
     ce = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "flag reset");
     const int nx = c->P.nx, ny = c->P.ny;
+    const size_t plane_bytes = (size_t)nx * ny * sizeof(double);
+    struct { double *h; int planes; } req[6] = {{rho, 1}, {u, 1}, {v, 1}, {T, 1}, {delta, 16}, {dstar, 16}};
+    double *dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool direct = planes > 0;
+    for (int k = 0; k < 6; k++) {
+        if (!req[k].h) continue;
+        dev[k] = static_cast<double *>(mapped_host(req[k].h, req[k].planes * plane_bytes));
+        direct = direct && dev[k];
+    }
+    if (direct) {
+        // page-locked host outputs: the moments kernel writes them over the host link itself
+        ce = lbm::launch_moments(c->P, c->prec, c->f[c->cur], 0, ny, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
+                                 c->flag, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "moments kernel");
+    }
     const int R = rows_per_chunk(c, planes > 0 ? planes : 1);
-    for (int r0 = 0; r0 < ny; r0 += R) {
+    for (int r0 = 0; r0 < ny && !direct; r0 += R) {
         const int rows = std::min(R, ny - r0);
         const size_t m = (size_t)rows * nx;
         double *p = c->stage;

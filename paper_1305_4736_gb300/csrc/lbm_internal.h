@@ -16,8 +16,10 @@ constexpr int kTotalsThreads = 256;
 
 // All launchers enqueue on `st` and return the launch status.
 // `prec` is the storage precision (0 = float64 f, 1 = float32 deviation g).
-cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows, int *bad,
-                        cudaStream_t st);
+// Initialisation of interior rows row0 .. row0+rows-1 from fields [rows][nx] (device or mapped host
+// addresses of the first of those rows); a bad cell sets *bad.
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *rho, const double *u, const double *v,
+                        const double *T, int row0, int rows, int *bad, cudaStream_t st);
 cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
 // Plain fused step with tiles of 32 x ty cells (ty = 4, 8 or 16).
 cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty = kTY);

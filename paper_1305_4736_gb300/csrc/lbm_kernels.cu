@@ -233,6 +233,46 @@ __device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, i
         gy = sy = my = along;
         if (edge == 0) { gx = -k; mx = k - 1; } else { gx = nx - 1 + k; mx = nx - k; }
         const int kind = P.edge[edge].kind;
+        if (kind <= 1 && ((nx | P.pitch | (int)(plane & 1)) & 1) == 0) {
+            // periodic / zero gradient with even nx, pitch and plane: the layer-1 thread copies
+            // both ghost columns of its row, 16 bytes per population (pair) plane.  Ghost columns
+            // x-lo: -2, -1 <- nx-2, nx-1 (periodic) or 0, 0; x-hi: nx, nx+1 <- 0, 1 or nx-1, nx-1.
+            if (k == 2) return;
+            const long long row = (long long)(along + OY) * P.pitch;
+            const long long cg2 = row + (edge == 0 ? OX - 2 : nx + OX);
+            if (kind == 0) {
+                const long long cs2 = row + (edge == 0 ? nx - 2 + OX : OX);
+                if constexpr (sizeof(R) == sizeof(float)) {
+                    float2 *f2p = reinterpret_cast<float2 *>(f);
+#pragma unroll
+                    for (int pr = 0; pr < 8; pr++)
+                        *reinterpret_cast<float4 *>(f2p + pr * plane + cg2) =
+                            *reinterpret_cast<const float4 *>(f2p + pr * plane + cs2);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ; q++)
+                        *reinterpret_cast<double2 *>(f + q * plane + cg2) =
+                            *reinterpret_cast<const double2 *>(f + q * plane + cs2);
+                }
+            } else {
+                const long long cs = row + (edge == 0 ? OX : nx - 1 + OX);
+                if constexpr (sizeof(R) == sizeof(float)) {
+                    float2 *f2p = reinterpret_cast<float2 *>(f);
+#pragma unroll
+                    for (int pr = 0; pr < 8; pr++) {
+                        const float2 v = f2p[pr * plane + cs];
+                        *reinterpret_cast<float4 *>(f2p + pr * plane + cg2) = make_float4(v.x, v.y, v.x, v.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ; q++) {
+                        const double v = f[q * plane + cs];
+                        *reinterpret_cast<double2 *>(f + q * plane + cg2) = make_double2(v, v);
+                    }
+                }
+            }
+            return;
+        }
         sx = (kind == 0) ? ((gx % n) + n) % n : (edge == 0 ? 0 : nx - 1);
     } else {
         const int j = idx - n_x;
@@ -311,33 +351,51 @@ __global__ void k_ghost_batch(const Params *__restrict__ Pall, const BatchGrid *
 }
 
 // ---------------------------------------------------------------------------
-// Initialisation from macroscopic fields (float64 arithmetic in both modes).
-// fields = [4][rows][nx] (rho, u, v, T) for interior rows row0 .. row0+rows-1.
-// ---------------------------------------------------------------------------
+// Initialisation from macroscopic fields.  rho, u, v, T: [rows][nx] for interior rows
+// row0 .. row0+rows-1 (device addresses, or mapped page-locked host memory).
+// float64 mode: f^eq in float64.  float32 deviation mode: the deviations drho, j and
+// dP = P - P0 are formed in float64 and the deviation g = f^eq - f^eq0 is evaluated from them
+// in float32 (the deviation form has no cancellation against the reference state, so the
+// result carries the error of its float32 storage and a few roundings more).
 // A cell with rho <= 0, T <= 0 or a non-finite value sets *bad and is not written.
+// ---------------------------------------------------------------------------
 template <typename R, bool Dev>
-__global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, const double *__restrict__ fields,
-                       int row0, int rows, int *bad)
+__global__ void k_init(const __grid_constant__ Params P, R *__restrict__ f, const double *__restrict__ rho_i,
+                       const double *__restrict__ u_i, const double *__restrict__ v_i,
+                       const double *__restrict__ T_i, int row0, int rows, int *bad)
 {
     const int nx = P.nx;
     const long long n = (long long)rows * nx;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int x = (int)(i % nx), y = row0 + (int)(i / nx);
-    const double rho = fields[i], ux = fields[n + i], uy = fields[2 * n + i], T = fields[3 * n + i];
+    const double rho = rho_i[i], ux = u_i[i], uy = v_i[i], T = T_i[i];
     if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(ux) || !isfinite(uy)) {
         atomicOr(bad, 1);
         return;
     }
-    const Coef<double> &C = P.cd;
-    const double drho = rho - C.rho0;
-    const double dP = rho * T - C.P0;
-    double q[NQ], g[NQ];
-    feq_hat_dev<double, Dev>(C, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
-    pop_from_moments(C, q, g);
     const long long c = (long long)(y + OY) * P.pitch + (x + OX);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const Coef<float> &C = P.cf;
+        const float drho = (float)(rho - P.cd.rho0);
+        const float dP = (float)fma(rho, T, -P.cd.P0);
+        const float jx = (float)(rho * ux), jy = (float)(rho * uy);
+        float q[NQ], g[NQ];
+        feq_hat_dev<float, Dev>(C, drho, jx, jy, dP, recip((float)rho), q);
+        pop_from_moments(C, q, g);
+        float2 *f2p = reinterpret_cast<float2 *>(f);
 #pragma unroll
-    for (int qq = 0; qq < NQ; qq++) f[pidx<R>(qq, P.plane, c)] = R(g[qq]);
+        for (int pr = 0; pr < 8; pr++) f2p[pr * P.plane + c] = make_float2(g[pair_q(pr)], g[pair_q(pr) + 4]);
+    } else {
+        const Coef<double> &C = P.cd;
+        const double drho = rho - C.rho0;
+        const double dP = rho * T - C.P0;
+        double q[NQ], g[NQ];
+        feq_hat_dev<double, Dev>(C, drho, rho * ux, rho * uy, dP, 1.0 / rho, q);
+        pop_from_moments(C, q, g);
+#pragma unroll
+        for (int qq = 0; qq < NQ; qq++) f[pidx<R>(qq, P.plane, c)] = R(g[qq]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -372,7 +430,8 @@ __device__ __forceinline__ void velocity_i(int i, double &vx, double &vy)
     vy = sgn_y(i) * sp[i >> 2];
 }
 
-template <typename R, bool Dev>
+// WantD = false: rho, u, v, T only (the conserved moments; delta_o and dstar_o are null).
+template <typename R, bool Dev, bool WantD>
 __global__ void k_moments(const __grid_constant__ Params P, const R *__restrict__ f, int row0, int rows,
                           double *rho_o, double *u_o, double *v_o, double *T_o, double *delta_o,
                           double *dstar_o, int *flag)
@@ -387,12 +446,27 @@ __global__ void k_moments(const __grid_constant__ Params P, const R *__restrict_
 #pragma unroll
     for (int q = 0; q < NQ; q++) g[q] = (double)f[pidx<R>(q, P.plane, c)];
     double rho, ux, uy, T, D[NQ], ir;
-    moment_rows<Dev>(P, g, rho, ux, uy, T, D, ir);
+    if constexpr (WantD) {
+        moment_rows<Dev>(P, g, rho, ux, uy, T, D, ir);
+    } else {
+        // the same expressions as moment_rows for these four
+        const Coef<double> &C = P.cd;
+        double drho, jx, jy, de;
+        conserved_of(shells_of(g), drho, jx, jy, de);
+        rho = Dev ? C.rho0 + drho : drho;
+        ir = 1.0 / rho;
+        ux = jx * ir;
+        uy = jy * ir;
+        const double J2 = jx * ux + jy * uy;
+        const double dP = (de - J2) * C.inv_b;
+        T = (Dev ? C.P0 + dP : dP) * ir;
+    }
     if (!(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(T)) atomicOr(flag, 1);
     if (rho_o) rho_o[i] = rho;
     if (u_o) u_o[i] = ux;
     if (v_o) v_o[i] = uy;
     if (T_o) T_o[i] = T;
+    if constexpr (!WantD) return;
     if (delta_o) {
 #pragma unroll
         for (int k = 0; k < NQ; k++) delta_o[k * n + i] = D[k];
@@ -563,13 +637,15 @@ __global__ void k_unpack(const __grid_constant__ Params P, R *__restrict__ f, in
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-cudaError_t launch_init(const Params &P, int prec, void *f, const double *fields, int row0, int rows, int *bad,
-                        cudaStream_t st)
+cudaError_t launch_init(const Params &P, int prec, void *f, const double *rho, const double *u, const double *v,
+                        const double *T, int row0, int rows, int *bad, cudaStream_t st)
 {
     const long long n = (long long)rows * P.nx;
     if (n == 0) return cudaSuccess;
-    if (prec == 0) k_init<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, fields, row0, rows, bad);
-    else k_init<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, fields, row0, rows, bad);
+    if (prec == 0)
+        k_init<double, false><<<blocks_for(n, 256), 256, 0, st>>>(P, (double *)f, rho, u, v, T, row0, rows, bad);
+    else
+        k_init<float, true><<<blocks_for(n, 256), 256, 0, st>>>(P, (float *)f, rho, u, v, T, row0, rows, bad);
     return cudaGetLastError();
 }
 
@@ -663,12 +739,20 @@ cudaError_t launch_moments(const Params &P, int prec, const void *f, int row0, i
 {
     const long long n = (long long)rows * P.nx;
     if (n == 0) return cudaSuccess;
-    if (prec == 0)
-        k_moments<double, false><<<blocks_for(n, 128), 128, 0, st>>>(P, (const double *)f, row0, rows, rho, u, v,
-                                                                    T, delta, dstar, flag);
+    const bool want_d = delta || dstar;
+    const dim3 g(blocks_for(n, 128)), b(128);
+    if (prec == 0 && want_d)
+        k_moments<double, false, true><<<g, b, 0, st>>>(P, (const double *)f, row0, rows, rho, u, v, T, delta, dstar,
+                                                        flag);
+    else if (prec == 0)
+        k_moments<double, false, false><<<g, b, 0, st>>>(P, (const double *)f, row0, rows, rho, u, v, T, nullptr,
+                                                         nullptr, flag);
+    else if (want_d)
+        k_moments<float, true, true><<<g, b, 0, st>>>(P, (const float *)f, row0, rows, rho, u, v, T, delta, dstar,
+                                                      flag);
     else
-        k_moments<float, true><<<blocks_for(n, 128), 128, 0, st>>>(P, (const float *)f, row0, rows, rho, u, v, T,
-                                                                  delta, dstar, flag);
+        k_moments<float, true, false><<<g, b, 0, st>>>(P, (const float *)f, row0, rows, rho, u, v, T, nullptr,
+                                                       nullptr, flag);
     return cudaGetLastError();
 }
 
