@@ -403,8 +403,62 @@ def serving_measure(count, steps, max_nx, max_ny, device, seed=1305):
             "one_at_a_time_fp64_solves_per_s": rate64, "speedup_vs_one_at_a_time_fp64": st.solves_per_s / rate64}
 
 
+def batch_measure(device, steps=20, warmup=3, seed=1305):
+    """Batched stepping (one lbm_batch: a ghost launch and a fused-step launch per step over a
+    tile list of all grids) of 24 uneven float32 shear-layer grids whose buffers exceed L2,
+    against stepping the same grids one at a time on their automatic kernels."""
+    import numpy as np
+    import torch
+    from paper_1305_4736_gb300 import lbm, workloads as wl
+    rng = np.random.default_rng(seed)
+    sizes = [(int(rng.choice([512, 768, 1024, 1536, 2048])), int(rng.choice([256, 384, 512, 768, 1024])))
+             for _ in range(24)]
+    solvers = []
+    for k, (nx, ny) in enumerate(sizes):
+        p = wl.shear_layer(nx, ny=ny, seed=seed + k)
+        s = lbm.Solver.from_problem(p, precision=1, device=device)
+        s.init(*p.fields())
+        solvers.append(s)
+    cells = sum(nx * ny for nx, ny in sizes)
+    stream = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn(warmup)
+        torch.cuda.synchronize(device)
+        ev0.record(stream)
+        fn(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(device)
+        return ev0.elapsed_time(ev1) / steps
+
+    b = lbm.Batch(solvers)
+    ms = timed(b.step)
+    b.close()
+
+    def solo(n):
+        for s in solvers:
+            s.step(n)
+    ms_solo = timed(solo)
+    for s in solvers:
+        s.close()
+    gbs = 128.0 * cells / (ms * 1e-3) / 1e9
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"grids": len(sizes), "cells": cells, "sizes": "nx 512..2048, ny 256..1024 (seeded)",
+            "dtype": "f32", "bytes_per_step": 128 * cells, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "peak_source": f"{peak_src} hbm_gbs", "traffic": None,
+                         "kernel": "k_ghost_batch, then each grid's k_step_tma<float,dev,MC> on 8 forked "
+                                   "streams (grids under 512 cells per SM: k_step_batch), in one CUDA graph"},
+            "one_at_a_time_ms_per_step": ms_solo, "speedup_vs_one_at_a_time": ms_solo / ms}
+
+
 def finish(line, p, args, rank, world):
     if rank == 0 and args.serving_requests > 0:
+        import torch
+        line["batch"] = batch_measure(torch.cuda.current_device())
         import torch
         line["serving"] = serving_measure(args.serving_requests, args.serving_steps, 1024, 256,
                                           torch.cuda.current_device())

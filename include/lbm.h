@@ -204,13 +204,17 @@ int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
    and one fused-step launch whose persistent CTAs walk a tile list (float32: 256-cell tiles,
    float64: 64-cell tiles, which spread small float64 grids over more SMs; 32 columns wide,
    or TX = the smallest power of two >= nx for narrower grids) across
-   the group's grids; the arithmetic per cell is that of the plain step kernel.  Pairs of
-   steps are replayed from a CUDA graph captured on the first call with n >= 2.
+   the group's grids; the arithmetic per cell is that of the plain step kernel.  A context
+   whose own step kernel is TMA-staged and which has at least 512 cells per SM takes part in
+   its group's ghost launch only, and steps with its own kernel, launched on one of eight
+   forked streams so that such grids overlap.  Pairs of steps are replayed from a CUDA
+   graph captured on the first call with n >= 2 (recaptured when a context on its own kernel
+   was stepped alone an odd number of times since).
    Results agree with stepping each context alone to round-off (the batched kernel reads
    its parameters from shared memory, and the compiler may contract multiply-adds
-   differently); tiles are independent, so a grid's result does not depend on the other
-   members of its batch (bit for bit).  Contexts may also be stepped alone between batch
-   steps.  Errors: LBM_ERR_ARG (NULL, empty, mixed device or stream, a
+   differently), and bit for bit for contexts on their own kernels; tiles are independent,
+   so a grid's result does not depend on the other members of its batch (bit for bit).
+   Contexts may also be stepped alone between batch steps.  Errors: LBM_ERR_ARG (NULL, empty, mixed device or stream, a
    context listed twice), LBM_ERR_STATE (uninitialised context, n <= 0), LBM_ERR_OOM,
    LBM_ERR_CUDA. */
 typedef struct lbm_batch lbm_batch;

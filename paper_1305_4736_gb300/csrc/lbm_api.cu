@@ -290,15 +290,13 @@ bool tma_ready(lbm_ctx *c)
     return lbm::tma_supported(c->P, c->prec) && lbm::tma_prepare() == cudaSuccess && make_tile_maps(c);
 }
 
-cudaError_t launch_fused_step(lbm_ctx *c)
+// One fused step of context c from buffer `in` into buffer in ^ 1, on stream st.
+cudaError_t launch_fused_step(lbm_ctx *c, int in, cudaStream_t st)
 {
-    if (c->use_pipe)
-        return lbm::launch_step_tma_pipe(c->P, &c->pmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
-    if (c->use_stream)
-        return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
-    if (c->use_tma)
-        return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
-    return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream, c->plain_ty);
+    if (c->use_pipe) return lbm::launch_step_tma_pipe(c->P, &c->pmap[in], c->f[in ^ 1], c->tma_err, st);
+    if (c->use_stream) return lbm::launch_step_stream(c->P, c->prec, &c->smap[in], c->f[in ^ 1], c->tma_err, st);
+    if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in ^ 1], c->tma_err, st);
+    return lbm::launch_step(c->P, c->prec, c->f[in], c->f[in ^ 1], st, c->plain_ty);
 }
 
 }  // namespace
@@ -620,7 +618,7 @@ int lbm_step(lbm_ctx *c, int n)
         ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
         if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
-        ce = launch_fused_step(c);
+        ce = launch_fused_step(c, c->cur, c->stream);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "step kernel");
         if (ev) cudaEventRecord(ev[3], c->stream);
         c->cur ^= 1;
@@ -929,6 +927,7 @@ struct lbm_batch {
     struct Group {
         int prec = 0, limiter = 0;
         std::vector<int> members;               // indices into ctxs
+        std::vector<char> own;                   // member steps on its own kernel (no tiles)
         std::vector<lbm::BatchGrid> hG;
         void *block = nullptr;                   // device: Params[n] | BatchGrid[n] | int4[ntiles]
         size_t bytes = 0;
@@ -940,6 +939,14 @@ struct lbm_batch {
     };
     std::vector<lbm_ctx *> ctxs;
     std::vector<Group> groups;
+    // contexts large enough for their own TMA-staged kernel (one wave of its tiles): their
+    // ghost cells come from their group's batched ghost launch, their step from that kernel,
+    // launched on kForks forked streams so that the grids' kernels overlap; their buffer parity
+    // at capture time
+    static constexpr int kForks = 8;
+    std::vector<int> solo, solo_cur;
+    cudaStream_t fork[kForks] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kForks] = {};
     cudaStream_t stream = nullptr, cap = nullptr;
     cudaGraphExec_t exec2 = nullptr;
     lbm_allocator alloc{};
@@ -961,14 +968,41 @@ cudaError_t batch_upload_cur(lbm_batch *b)
 
 cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
 {
+    cudaError_t ce = cudaSuccess;
     for (auto &g : b->groups) {
-        cudaError_t ce = lbm::launch_ghost_batch(g.dP, g.dG, (int)g.members.size(), g.max_ghost, g.prec, phase, st);
-        if (ce == cudaSuccess)
-            ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
-                                        g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
+        ce = lbm::launch_ghost_batch(g.dP, g.dG, (int)g.members.size(), g.max_ghost, g.prec, phase, st);
         if (ce != cudaSuccess) return ce;
     }
-    return cudaSuccess;
+    const int nf = std::min<int>(lbm_batch::kForks, (int)b->solo.size());
+    if (nf > 0) {
+        ce = cudaEventRecord(b->ev_fork, st);
+        for (int k = 0; k < nf && ce == cudaSuccess; k++) ce = cudaStreamWaitEvent(b->fork[k], b->ev_fork, 0);
+        if (ce != cudaSuccess) return ce;
+    }
+    for (auto &g : b->groups) {
+        ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
+                                    g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
+        if (ce != cudaSuccess) return ce;
+    }
+    for (size_t j = 0; j < b->solo.size(); j++) {
+        lbm_ctx *c = b->ctxs[b->solo[j]];
+        ce = launch_fused_step(c, c->cur ^ phase, b->fork[j % lbm_batch::kForks]);
+        if (ce != cudaSuccess) return ce;
+    }
+    for (int k = 0; k < nf && ce == cudaSuccess; k++) {
+        ce = cudaEventRecord(b->ev_join[k], b->fork[k]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, b->ev_join[k], 0);
+    }
+    return ce;
+}
+
+// A context runs its own TMA-staged kernel inside the batch when it has one and fills at
+// least a quarter of a wave of that kernel's tiles (512 cells per SM; the forked streams let
+// several such kernels share the SMs); smaller grids share the packed tile kernel, where one
+// launch serves them all.
+bool batch_solo(const lbm_ctx *c, int sms)
+{
+    return (c->use_tma || c->use_stream || c->use_pipe) && (long long)c->P.nx * c->P.ny >= 512LL * sms;
 }
 
 }  // namespace
@@ -1000,6 +1034,8 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
     b->ctas = 4 * sms;
     for (int i = 0; i < n; i++) {
         const lbm_ctx *c = ctxs[i];
+        const bool own = batch_solo(c, sms);
+        if (own) b->solo.push_back(i);
         lbm_batch::Group *g = nullptr;
         for (auto &gg : b->groups)
             if (gg.prec == c->prec && gg.limiter == c->P.limiter) g = &gg;
@@ -1010,13 +1046,15 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             g->limiter = c->P.limiter;
         }
         g->members.push_back(i);
+        g->own.push_back(own ? 1 : 0);
     }
     for (auto &g : b->groups) {
         // float64 groups too small to give every SM four 256-cell tiles take 64-cell tiles,
         // which spread their float64 work over more SMs
         if (g.prec == LBM_FP64) {
             long long cells = 0;
-            for (int m : g.members) cells += (long long)b->ctxs[m]->P.nx * b->ctxs[m]->P.ny;
+            for (size_t k = 0; k < g.members.size(); k++)
+                if (!g.own[k]) cells += (long long)b->ctxs[g.members[k]]->P.nx * b->ctxs[g.members[k]]->P.ny;
             g.nt = cells >= 4LL * lbm::kBatchThreads * sms ? lbm::kBatchThreads : lbm::kBatchThreadsFp64;
         }
         std::vector<int4> tiles;
@@ -1026,6 +1064,7 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             hp.push_back(c->P);
             g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
+            if (g.own[k]) continue;                  // ghost cells only
             const int lt = lbm::plain_log_tx(c->P.nx);
             const int nt = g.nt;
             const int tw = 1 << lt, th = nt >> lt;
@@ -1052,6 +1091,11 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
         if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "batch tables"); }
     }
     ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < lbm_batch::kForks && ce == cudaSuccess; k++) {
+        ce = cudaStreamCreateWithFlags(&b->fork[k], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+    }
     if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "capture stream"); }
     *out = b;
     return LBM_OK;
@@ -1067,7 +1111,21 @@ int lbm_batch_step(lbm_batch *b, int n)
     cudaError_t ce = cudaSetDevice(b->device);
     if (ce == cudaSuccess) ce = batch_upload_cur(b);
     if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch");
+    if (b->exec2) {
+        // the graph's own-kernel launches name their buffers: recapture if a context was
+        // stepped alone an odd number of times since the capture
+        bool same = true;
+        for (size_t k = 0; k < b->solo.size(); k++) same = same && b->ctxs[b->solo[k]]->cur == b->solo_cur[k];
+        if (!same) {
+            ce = cudaStreamSynchronize(b->stream);
+            if (ce == cudaSuccess) ce = cudaGraphExecDestroy(b->exec2);
+            b->exec2 = nullptr;
+            if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch graph");
+        }
+    }
     if (n >= 2 && !b->exec2) {
+        b->solo_cur.clear();
+        for (int i : b->solo) b->solo_cur.push_back(b->ctxs[i]->cur);
         // capture two steps (both buffer parities) once; replays read the tables' current contents
         cudaGraph_t graph = nullptr;
         ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
@@ -1101,6 +1159,11 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaStreamSynchronize(b->stream);
     if (b->exec2) cudaGraphExecDestroy(b->exec2);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < lbm_batch::kForks; k++) {
+        if (b->fork[k]) cudaStreamDestroy(b->fork[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     for (auto &g : b->groups)
         if (g.block && b->alloc.free) b->alloc.free(g.block, g.bytes, b->stream, b->alloc.user);
     delete b;
