@@ -723,8 +723,14 @@ int lbm_get_state(lbm_ctx *c, double *f)
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     const int nx = c->P.nx, ny = c->P.ny;
+    // page-locked host array: the pack kernel writes it over the host link itself
+    double *dev = static_cast<double *>(mapped_host(f, (size_t)NQ * nx * ny * sizeof(double)));
+    if (dev) {
+        ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], 0, ny, dev, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "pack kernel");
+    }
     const int R = rows_per_chunk(c, 16);
-    for (int r0 = 0; r0 < ny; r0 += R) {
+    for (int r0 = 0; r0 < ny && !dev; r0 += R) {
         const int rows = std::min(R, ny - r0);
         const size_t m = (size_t)rows * nx;
         ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], r0, rows, c->stage, c->stream);
@@ -749,8 +755,13 @@ int lbm_get_state_rows(lbm_ctx *c, int row0, int rows, double *f)
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     const int nx = c->P.nx;
+    double *dev = static_cast<double *>(mapped_host(f, (size_t)NQ * nx * rows * sizeof(double)));
+    if (dev) {
+        ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], row0, rows, dev, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "pack kernel");
+    }
     const int R = rows_per_chunk(c, 16);
-    for (int r = 0; r < rows; r += R) {
+    for (int r = 0; r < rows && !dev; r += R) {
         const int n = std::min(R, rows - r);
         const size_t m = (size_t)n * nx;
         ce = lbm::launch_pack(c->P, c->prec, c->f[c->cur], row0 + r, n, c->stage, c->stream);
@@ -773,8 +784,14 @@ int lbm_set_state(lbm_ctx *c, const double *f)
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     const int nx = c->P.nx, ny = c->P.ny;
+    // page-locked host array: the unpack kernel reads it over the host link itself
+    const double *dev = static_cast<const double *>(mapped_host(f, (size_t)NQ * nx * ny * sizeof(double)));
+    if (dev) {
+        ce = lbm::launch_unpack(c->P, c->prec, c->f[c->cur], 0, ny, dev, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "unpack kernel");
+    }
     const int R = rows_per_chunk(c, 16);
-    for (int r0 = 0; r0 < ny; r0 += R) {
+    for (int r0 = 0; r0 < ny && !dev; r0 += R) {
         const int rows = std::min(R, ny - r0);
         const size_t m = (size_t)rows * nx;
         for (int q = 0; q < NQ; q++) {

@@ -105,3 +105,29 @@ def test_fp32_initial_state_against_oracle(orc, lbm, name):
     # float32 evaluation and storage of g stay within 1e-6 of that spread
     spread = np.abs(fo - fo.mean(axis=(1, 2), keepdims=True)).max()
     assert np.abs(got - fo).max() <= 1e-6 * max(spread, 1e-3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_round_trip_through_pinned_memory(lbm, precision):
+    """lbm_get_state, lbm_get_state_rows and lbm_set_state on page-locked arrays give the
+    staged route's results bit for bit."""
+    p = wl.shear_layer(700, ny=1300, seed=7)          # 0.9 M cells: two staging chunks of 16 planes
+    s = lbm.Solver.from_problem(p, precision=precision)
+    s.init(*p.fields())
+    s.step(3)
+    want = s.get_state()
+    got, _t = _pinned(want.shape)
+    lbm.lbm_get_state(s.h, got)
+    assert np.array_equal(got, want)
+    rows, _r = _pinned((16, 301, p.nx))
+    lbm.lbm_get_state_rows(s.h, 555, 301, rows)
+    assert np.array_equal(rows, want[:, 555:856])
+    # write back a perturbed state through the pinned route, read it through the staged route
+    new, _n = _pinned(want.shape, want * (1.0 + 1e-3))
+    lbm.lbm_set_state(s.h, new)
+    back = s.get_state()
+    t = lbm.Solver.from_problem(p, precision=precision)
+    t.set_state(np.array(new))
+    assert np.array_equal(back, t.get_state())
+    s.close()
+    t.close()
