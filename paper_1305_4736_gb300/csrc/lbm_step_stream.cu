@@ -205,7 +205,6 @@ __device__ __forceinline__ void win_init(Win<float> &W, const float2 *a, const f
                                          const float2 *d)
 {
     constexpr int BW = StreamShape<float>::BW;
-    const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
     for (int pr = 0; pr < 8; pr++) {
         const int sy = tsgn_y(pair_q(pr));
@@ -220,7 +219,7 @@ __device__ __forceinline__ void win_init(Win<float> &W, const float2 *a, const f
             const float2 d1 = sub2(c[o], b[o]), d2 = sub2(d[o], c[o]);
             W.w[pr] = d[o];
             W.d[pr] = d2;
-            W.m[pr] = slope2x2<Lim>(mul2(d2, m1), mul2(d1, m1));
+            W.m[pr] = slope2x2<Lim>(d2, d1);   // the oriented slope, negated (slope2x2 is odd)
         }
     }
 }
@@ -257,7 +256,6 @@ __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &
                                               float *__restrict__ fout, long long plane, long long cg)
 {
     constexpr int BW = StreamShape<float>::BW;
-    const float2 m1 = f2(-1.f, -1.f);
     float2 *out2 = reinterpret_cast<float2 *>(fout);
 #pragma unroll
     for (int pr = 0; pr < 8; pr++) {
@@ -278,10 +276,9 @@ __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &
                 tyv = Lim == 2 ? W.d[pr] : fma2(hy, sub2(mn, W.m[pr]), W.d[pr]);
                 W.m[pr] = mn;
             } else {
-                // flux -D(y+1) + h (slope_y - slope_{y+1})
-                const float2 nd = mul2(W.d[pr], m1);
-                const float2 mn = slope2x2<Lim>(mul2(dn, m1), nd);
-                tyv = Lim == 2 ? nd : fma2(hy, sub2(W.m[pr], mn), nd);
+                // flux -D(y+1) + h (slope_y - slope_{y+1}), carried negated with negated slopes
+                const float2 mn = slope2x2<Lim>(dn, W.d[pr]);
+                tyv = Lim == 2 ? W.d[pr] : fma2(hy, sub2(W.m[pr], mn), W.d[pr]);
                 W.m[pr] = mn;
             }
             W.w[pr] = wn;
@@ -289,7 +286,8 @@ __device__ __forceinline__ void convect_store(const Coef<float> &C, Win<float> &
         }
         // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
         float2 out = sub2(f0, acc[pr]);
-        if (sy != 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+        if (sy > 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+        if (sy < 0) out = fma2(ld2(&C.cry[sa]), tyv, out);
         if (sx != 0) out = fma2(ld2(&C.ncr[sa]), tx, out);
         if (store) out2[pr * plane + cg] = out;
     }

@@ -30,7 +30,6 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
     const Coef<float> &C = coef<float>(P);
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
-    const float2 m1 = f2(-1.f, -1.f);
     const float2 *col = tile + (lane + S::HX);
     // sliding y-window state per y-moving pair: last value, face difference, slope
     float2 yw[8], yd[8], ym[8];
@@ -46,11 +45,12 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
             yd[pr] = d1;
             ym[pr] = slope2x2<Lim>(d0, d1);
         } else {
+            // downward pairs carry their oriented slope negated (slope2x2 is odd): no negations
             const float2 w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
             const float2 d1 = sub2(w2, w1), d2 = sub2(w3, w2);
             yw[pr] = w3;
             yd[pr] = d2;
-            ym[pr] = slope2x2<Lim>(mul2(d2, m1), mul2(d1, m1));
+            ym[pr] = slope2x2<Lim>(d2, d1);
         }
     }
     float2 *out2 = reinterpret_cast<float2 *>(fout);
@@ -91,9 +91,9 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
                     tyv = Lim == 2 ? yd[pr] : fma2(hy, sub2(mn, ym[pr]), yd[pr]);
                     ym[pr] = mn;
                 } else {
-                    const float2 nyd = mul2(yd[pr], m1);
-                    const float2 mn = slope2x2<Lim>(mul2(dn, m1), nyd);
-                    tyv = Lim == 2 ? nyd : fma2(hy, sub2(ym[pr], mn), nyd);
+                    // the flux negated: D(y+1) + h (slope'_{y+1} - slope'_y) with negated slopes
+                    const float2 mn = slope2x2<Lim>(dn, yd[pr]);
+                    tyv = Lim == 2 ? yd[pr] : fma2(hy, sub2(ym[pr], mn), yd[pr]);
                     ym[pr] = mn;
                 }
                 yw[pr] = wn;
@@ -101,7 +101,8 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
             }
             // f - C - c_x (F_out - F_in)_x - c_y (F_out - F_in)_y
             float2 out = sub2(f0, acc[pr]);
-            if (sy != 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+            if (sy > 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
+            if (sy < 0) out = fma2(ld2(&C.cry[sa]), tyv, out);
             if (sx != 0) out = fma2(ld2(&C.ncr[sa]), tx, out);
             if (store) out2[pr * P.plane + cg] = out;
         }
