@@ -251,12 +251,17 @@ def _patch(f_rows, y_local, x, nx):
     return out
 
 
-@pytest.mark.parametrize("prec", [0])
+@pytest.mark.parametrize("prec", [0, 1])
 def test_full_size_shear_layer_sampled(orc, lbm, prec):
-    """8192 x 8192 shear layer in the benchmark's launch configuration: after 3 steps,
-    64 seeded cells of step 4 are recomputed by the oracle from the GPU's step-3 state."""
+    """8192 x 8192 shear layer in the benchmark's launch configuration (float64: the streaming
+    kernel; float32 deviation mode: the TMA-staged tile kernel): after 3 steps, 64 seeded cells
+    of step 4 are recomputed by the oracle from the GPU's step-3 state.  float64: 1e-13 of f.
+    float32: 1e-6 of f, and per cell 2^-20 (8 float32 ulps) of the cell's largest stored
+    deviation |g| = |f - f^eq0| (measured: under 2 ulps).  That is about 1% of the largest
+    change of f in the step here, so a dropped or wrong term of the update fails."""
     p = wl.shear_layer(8192)
     s = lbm.Solver.from_problem(p, precision=prec)
+    assert s.step_kernel == (5 if prec == 0 else 2)
     s.init(*p.fields())
     s.step(3)
     rng = np.random.default_rng(7)
@@ -264,13 +269,23 @@ def test_full_size_shear_layer_sampled(orc, lbm, prec):
     xs = rng.integers(0, p.nx, 64)
     before = {int(y): s.get_state_rows(int(y) - 2, 5) for y in set(ys.tolist())}
     s.step(1)
-    worst = 0.0
+    O = orc.Oracle(4, 4, p.dx, p.dt, p.gamma, p.s, p.limiter, wl.periodic_bc())
+    O.init(np.ones((4, 4)), np.zeros((4, 4)), np.zeros((4, 4)), np.ones((4, 4)))
+    feq0 = O.get_state()[:, 0, 0]                      # the float32 mode's reference (1, 0, 0, 1)
+    worst, worst_g, largest_change = 0.0, 0.0, 0.0
     for y, x in zip(ys.tolist(), xs.tolist()):
         want = orc.update_patch(_patch(before[y], 2, x, p.nx), p.dx, p.dt, p.gamma, p.s, p.limiter)
         got = s.get_state_rows(y, 1)[:, 0, x]
+        prev = before[y][:, 2, x]
         worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
+        worst_g = max(worst_g, np.abs(got - want).max() / np.abs(prev - feq0).max())
+        largest_change = max(largest_change, np.abs(want - prev).max())
     s.close()
-    assert worst <= 1e-13
+    if prec == 0:
+        assert worst <= 1e-13
+    else:
+        assert worst <= 1e-6
+        assert worst_g <= 2.0 ** -20, (worst_g, largest_change)
 
 
 # ------------------------------------------------------------------ TMA-staged kernel == plain kernel
