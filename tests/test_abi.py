@@ -59,6 +59,8 @@ def _create_rc(lib, **kw):
     (dict(gamma=1.0), -1), (dict(Pr=0.0), -1), (dict(limiter=7), -1),
     (dict(dt=1e-3, s=np.full(16, 100.0)), -2),             # 6 dt/dx = 1.2 > 1
     (dict(s=np.full(16, 3e4)), -3),                        # s dt = 3 >= 2
+    (dict(nx=1 << 16, ny=1 << 15), -1),                     # 2^31 cells: above the grid limit
+    (dict(nx=(1 << 28) + 1, ny=1), -1),                     # a side above 2^28
 ])
 def test_create_rejects_bad_arguments(lib, kw, code):
     rc, msg = _create_rc(lib, **kw)
