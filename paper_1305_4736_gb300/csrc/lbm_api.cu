@@ -290,12 +290,16 @@ bool tma_ready(lbm_ctx *c)
     return lbm::tma_supported(c->P, c->prec) && lbm::tma_prepare() == cudaSuccess && make_tile_maps(c);
 }
 
+// The TMA-staged tile kernel takes the x halo of tiles at a periodic x edge from the wrapped
+// interior itself: on a grid periodic in x it needs only the ghost rows.
+bool ghost_rows_only(const lbm_ctx *c) { return c->use_tma && (c->P.wrap & 1); }
+
 // One fused step of context c from buffer `in` into buffer in ^ 1, on stream st.
 cudaError_t launch_fused_step(lbm_ctx *c, int in, cudaStream_t st)
 {
     if (c->use_pipe) return lbm::launch_step_tma_pipe(c->P, &c->pmap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_stream) return lbm::launch_step_stream(c->P, c->prec, &c->smap[in], c->f[in ^ 1], c->tma_err, st);
-    if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in ^ 1], c->tma_err, st);
+    if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
     return lbm::launch_step(c->P, c->prec, c->f[in], c->f[in ^ 1], st, c->plain_ty);
 }
 
@@ -393,6 +397,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     const double k8 = (s[7] == s[4]) ? 0.0 : s[7] / s[4] - 1.0;
     const double k9 = (s[8] == s[4]) ? 0.0 : s[8] / s[4] - 1.0;
     P.has_c9 = (k8 != 0.0 || k9 != 0.0) ? 1 : 0;
+    P.wrap = (bc->xlo.kind == LBM_BC_PERIODIC ? 1 : 0) | (bc->ylo.kind == LBM_BC_PERIODIC ? 2 : 0);
     C.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
     C.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
     C.ry = dx / dy;
@@ -615,7 +620,7 @@ int lbm_step(lbm_ctx *c, int n)
         cudaEvent_t *ev = nullptr;
         if (c->prof && c->prof_used < c->prof_max) ev = &c->prof_ev[4 * c->prof_used++];
         if (ev) cudaEventRecord(ev[0], c->stream);
-        ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream);
+        ce = lbm::launch_ghost(c->P, c->prec, c->f[c->cur], c->stream, ghost_rows_only(c));
         if (ce != cudaSuccess) return cuda_fail(c, ce, "ghost kernel");
         if (ev) { cudaEventRecord(ev[1], c->stream); cudaEventRecord(ev[2], c->stream); }
         ce = launch_fused_step(c, c->cur, c->stream);
@@ -902,7 +907,8 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
                 return lbm::launch_step_stream(c->P, c->prec, &c->smap[c->cur], c->f[c->cur ^ 1], c->tma_err,
                                                c->stream);
             if (cd == 2)
-                return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
+                return lbm::launch_step_tma(c->P, c->prec, &c->tmap[c->cur], c->f[c->cur], c->f[c->cur ^ 1], c->tma_err,
+                                            c->stream);
             return lbm::launch_step(c->P, c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->stream,
                                     cd == 3 ? 4 : (cd == 4 ? 16 : (cd == 7 ? 2 : 8)));
         };

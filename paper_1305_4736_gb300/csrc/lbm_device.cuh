@@ -80,6 +80,7 @@ struct EdgeDev {
 
 struct Params {
     int nx, ny, pitch, limiter, has_c9;
+    int wrap;                   // periodic axes: bit 0 x (x-lo and x-hi), bit 1 y
     long long plane;            // elements per population plane
     double dt, T0;
     double feq0[NQ];            // reference populations f^eq(rho0, 0, 0, T0) (deviation mode)

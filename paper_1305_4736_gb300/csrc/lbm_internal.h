@@ -20,7 +20,8 @@ constexpr int kTotalsThreads = 256;
 // addresses of the first of those rows); a bad cell sets *bad.
 cudaError_t launch_init(const Params &P, int prec, void *f, const double *rho, const double *u, const double *v,
                         const double *T, int row0, int rows, int *bad, cudaStream_t st);
-cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st);
+// Ghost cells of every edge, or (y_only) of the y edges only: the ghost rows.
+cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st, bool y_only = false);
 // Plain fused step with tiles of 32 x ty cells (ty = 4, 8 or 16).
 cudaError_t launch_step(const Params &P, int prec, const void *fin, void *fout, cudaStream_t st, int ty = kTY);
 // log2 of the plain kernels' tile width for a grid nx columns wide (5 for nx >= 32, else the
@@ -76,8 +77,11 @@ struct TmaShape {
 };
 bool tma_supported(const Params &P, int prec);
 cudaError_t tma_prepare();   // opt the kernels in to their dynamic shared memory (once per device)
-// `tmap` points to the CUtensorMap of the input buffer (3-D: pitch x (ny+4) x 16).
-cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);
+// `tmap` points to the CUtensorMap of the input buffer fin (3-D: pitch x (ny+4) x 16).  Tiles at a
+// periodic x edge take their x halo from the wrapped interior of fin, so on a grid periodic in x
+// the kernel needs only the ghost rows (launch_ghost with y_only).
+cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, const void *fin, void *fout, int *err,
+                            cudaStream_t st);
 
 // Persistent double-buffered TMA-staged kernel (float32): CTAs walk tiles of kTmaTX columns
 // by TR rows round-robin with two tile buffers, so that the copy of the next tile overlaps

@@ -332,10 +332,11 @@ __device__ __forceinline__ void ghost_cell(const Params &P, R *__restrict__ f, i
     }
 }
 
+// first: index of the first ghost cell handled (0: every edge; 4 ny: the y edges only)
 template <typename R, bool Dev>
-__global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f)
+__global__ void k_ghost(const __grid_constant__ Params P, R *__restrict__ f, int first)
 {
-    ghost_cell<R, Dev>(P, f, blockIdx.x * blockDim.x + threadIdx.x);
+    ghost_cell<R, Dev>(P, f, first + blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Batched ghost fill: blockIdx.y selects the grid of the batch.
@@ -649,11 +650,12 @@ cudaError_t launch_init(const Params &P, int prec, void *f, const double *rho, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st)
+cudaError_t launch_ghost(const Params &P, int prec, void *f, cudaStream_t st, bool y_only)
 {
-    const int n = 4 * (P.nx + P.ny);
-    if (prec == 0) k_ghost<double, false><<<blocks_for(n, 128), 128, 0, st>>>(P, (double *)f);
-    else k_ghost<float, true><<<blocks_for(n, 128), 128, 0, st>>>(P, (float *)f);
+    const int first = y_only ? 4 * P.ny : 0;
+    const int n = 4 * (P.nx + P.ny) - first;
+    if (prec == 0) k_ghost<double, false><<<blocks_for(n, 128), 128, 0, st>>>(P, (double *)f, first);
+    else k_ghost<float, true><<<blocks_for(n, 128), 128, 0, st>>>(P, (float *)f, first);
     return cudaGetLastError();
 }
 

@@ -109,10 +109,38 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
     }
 }
 
+// x halo of a tile at a periodic x edge: the staged cells left of column 0 or right of column
+// nx-1 (the ghost columns, and columns beyond them in a ragged last tile) take the values of
+// the wrapped interior cells of fin, as the periodic ghost fill would have written them.  The
+// ghost rows come from the ghost fill (contiguous rows, cheap to copy); cells outside along
+// both axes are corners of the ring, which the cross stencil of stored cells never reads.
+template <typename R>
+__device__ __noinline__ void wrap_halo(const Params &P, const R *__restrict__ fin, R *tile, int x0, int y0, int tid,
+                                       int nthreads)
+{
+    using S = TmaShape<R>;
+    for (int k = tid; k < S::SW * S::SH; k += nthreads) {
+        const int c = k % S::SW, r = k / S::SW;
+        const int x = x0 + c - S::HX, y = y0 + r - 2;
+        if (!(x < 0 || x >= P.nx) || y < 0 || y >= P.ny) continue;
+        const int xs = ((x % P.nx) + P.nx) % P.nx;
+        const long long src = (long long)(y + OY) * P.pitch + (xs + OX);
+        if constexpr (sizeof(R) == sizeof(float)) {
+            const float2 *f2 = reinterpret_cast<const float2 *>(fin);
+            float2 *t2 = reinterpret_cast<float2 *>(tile);
+#pragma unroll
+            for (int pr = 0; pr < 8; pr++) t2[pr * S::PL + k] = f2[pr * P.plane + src];
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; q++) tile[q * S::PL + k] = fin[q * P.plane + src];
+        }
+    }
+}
+
 template <typename R, bool Dev, int Lim>
 __global__ void __launch_bounds__(kTmaTX * TmaShape<R>::TT, TmaShape<R>::CTAS)
-k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, R *__restrict__ fout,
-           int *err)
+k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, const R *__restrict__ fin,
+           R *__restrict__ fout, int *err)
 {
     using S = TmaShape<R>;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -162,6 +190,11 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
             mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
         }
         return;
+    }
+    // tiles whose staged box reaches past a periodic x edge (uniform per CTA)
+    if ((P.wrap & 1) && (x0 < S::HX || x0 + kTmaTX + S::HX > nx)) {
+        wrap_halo<R>(P, fin, tile, x0, y0, tid, kTmaTX * S::TT);
+        __syncthreads();
     }
     const Coef<R> &C = coef<R>(P);
     // ---- phase 1: flow velocity and 1/rho on the tile plus its ring.  Cells of the ring
@@ -423,25 +456,28 @@ bool tma_supported(const Params &P, int prec)
     return P.pitch >= TmaShape<float>::SW && P.ny + 4 >= sh && P.nx >= kTmaTX;
 }
 
-cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st)
+cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, const void *fin, void *fout, int *err,
+                            cudaStream_t st)
 {
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
     if (prec == 0) {
         using S = TmaShape<double>;
         const dim3 block(kTmaTX, S::TT);
         const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
+        const double *a = (const double *)fin;
         double *b = (double *)fout;
-        if (P.limiter == 0) k_step_tma<double, false, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
-        else if (P.limiter == 1) k_step_tma<double, false, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
-        else k_step_tma<double, false, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
+        if (P.limiter == 0) k_step_tma<double, false, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        else if (P.limiter == 1) k_step_tma<double, false, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        else k_step_tma<double, false, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
     } else {
         using S = TmaShape<float>;
         const dim3 block(kTmaTX, S::TT);
         const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
+        const float *a = (const float *)fin;
         float *b = (float *)fout;
-        if (P.limiter == 0) k_step_tma<float, true, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
-        else if (P.limiter == 1) k_step_tma<float, true, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
-        else k_step_tma<float, true, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, b, err);
+        if (P.limiter == 0) k_step_tma<float, true, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        else if (P.limiter == 1) k_step_tma<float, true, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        else k_step_tma<float, true, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
     }
     return cudaGetLastError();
 }

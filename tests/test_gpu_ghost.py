@@ -63,3 +63,67 @@ def test_fp32_x_ghost_against_oracle(orc, lbm, nx, edges):
     s.close()
     for a, b in ((g[0], r[0]), (g[3], r[3])):
         assert l1_rel(a, b) <= 1e-4 and max_rel(a, b) <= 1e-3
+
+
+# ---- the TMA-staged tile kernel without ghost fill on periodic grids
+def _periodic(nx, ny, seed=14):
+    p = wl.shear_layer(max(nx, ny), seed=seed, steps=40)
+    p.nx, p.ny = nx, ny
+    p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:ny, :nx]) for a in (p.rho, p.ux, p.uy, p.T))
+    p.ux = p.ux + 0.02
+    return p
+
+
+def _tma(lbm, p, precision, kernel=2):
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter, p.bc, precision=precision,
+                   step_kernel=kernel)
+    s.init(*p.fields())
+    return s
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 32), (33, 35), (70, 50)])
+def test_fp64_tile_kernel_wraps_periodic_edges(orc, lbm, nx, ny):
+    """Tiles at a periodic edge take their halo from the wrapped interior (no ghost fill on a
+    doubly periodic grid); the smallest grid of one tile and ragged grids, against the oracle."""
+    p = _periodic(nx, ny)
+    s = _tma(lbm, p, 0)
+    s.step(40)
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*p.fields())
+    O.step(40)
+    fo = O.get_state()
+    got = s.get_state()
+    s.close()
+    assert np.abs(got - fo).max() <= TOL * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 16), (33, 17), (45, 30), (96, 64)])
+def test_fp32_tile_kernel_wraps_periodic_edges(lbm, nx, ny):
+    p = _periodic(nx, ny)
+    a, b = _tma(lbm, p, 1, kernel=1), _tma(lbm, p, 1, kernel=2)
+    a.step(40)
+    b.step(40)
+    want, got = a.get_state(), b.get_state()
+    a.close()
+    b.close()
+    assert np.abs(got - want).max() <= 2e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_kernel_periodic_in_x_walls_in_y(orc, lbm, precision):
+    """One periodic axis: the x halo wraps in the kernel, the y walls come from the ghost fill."""
+    p = _periodic(64, 40)
+    p.bc = [P, P, (wl.BC_NEQ_WALL, 1.0, 0.01, 0.0, 1.0), (wl.BC_NEQ_WALL, 1.0, -0.02, 0.0, 1.01)]
+    s = _tma(lbm, p, precision)
+    s.step(40)
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*p.fields())
+    O.step(40)
+    if precision == 0:
+        fo = O.get_state()
+        assert np.abs(s.get_state() - fo).max() <= TOL * np.abs(fo).max()
+    else:
+        g, r = s.moments(), O.moments()
+        for a, b in ((g[0], r[0]), (g[3], r[3])):
+            assert l1_rel(a, b) <= 1e-4 and max_rel(a, b) <= 1e-3
+    s.close()
