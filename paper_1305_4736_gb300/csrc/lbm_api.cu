@@ -397,7 +397,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     const double k8 = (s[7] == s[4]) ? 0.0 : s[7] / s[4] - 1.0;
     const double k9 = (s[8] == s[4]) ? 0.0 : s[8] / s[4] - 1.0;
     P.has_c9 = (k8 != 0.0 || k9 != 0.0) ? 1 : 0;
-    P.wrap = (bc->xlo.kind == LBM_BC_PERIODIC ? 1 : 0) | (bc->ylo.kind == LBM_BC_PERIODIC ? 2 : 0);
+
     C.q8 = (k8 != 0.0) ? k8 / s[7] / (2.0 * dx) : 0.0;
     C.q9 = (k9 != 0.0) ? k9 / s[8] / (2.0 * dx) : 0.0;
     C.ry = dx / dy;
@@ -504,6 +504,16 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     // and then to the plain kernel where the grid or driver does not allow it
     if ((want == 5 || (want == 0 && prec == LBM_FP64)) && stream_ready(c)) c->use_stream = true;
     if ((want == 2 || (want == 0 && !c->use_stream)) && tma_ready(c)) c->use_tma = true;
+    // x halo of periodic edge tiles wrapped inside the TMA-staged tile kernel (P.wrap bit 0), on
+    // grids of at least 32 waves of its tiles (2048 cells per SM a wave): there the kernel's
+    // extra loads in edge tiles cost less than the ghost columns' copy; on smaller grids a
+    // kernel lasts as long as its slowest tiles, which the extra loads lengthen
+    if (c->use_tma && bc->xlo.kind == LBM_BC_PERIODIC) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (sms < 1) sms = 152;
+        if ((long long)nx * ny >= 32LL * 2048 * sms) c->P.wrap = 1;
+    }
     if (want == 6 && pipe_ready(c)) c->use_pipe = true;
     if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream) || (want == 6 && !c->use_pipe)) {
         lbm_destroy(c);

@@ -80,7 +80,7 @@ struct EdgeDev {
 
 struct Params {
     int nx, ny, pitch, limiter, has_c9;
-    int wrap;                   // periodic axes: bit 0 x (x-lo and x-hi), bit 1 y
+    int wrap;                   // bit 0: the tile kernel wraps the x halo of periodic edge tiles
     long long plane;            // elements per population plane
     double dt, T0;
     double feq0[NQ];            // reference populations f^eq(rho0, 0, 0, T0) (deviation mode)
