@@ -122,6 +122,38 @@ __device__ __forceinline__ void halo_velocity(const Coef<R> &C, const R *p, R cx
     v = by * ir;
 }
 
+// float64: the flow velocities of halo_velocity for two rows at once, the cell at p (row y) and
+// the cell at q (row y+1).  The first level of the 16-lane reductions serves both rows: lanes
+// with bit 3 clear go on with row y, the others with row y+1, and the reciprocal and the
+// divisions run once for both.  Every lane of a pair adds the same two partial sums, so the
+// sums are those of halo_velocity bit for bit.  u0, v0: row y of this lane's column (lanes 0-15
+// the left one, 16-31 the right one); u1, v1: row y+1.
+__device__ __forceinline__ void halo_velocity2(const double *p, const double *q, double cx, double cy, int lane,
+                                               double &u0, double &v0, double &u1, double &v1)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const double ga = *p, gb = *q;
+    const double xa = cx * ga, ya = cy * ga, xb = cx * gb, yb = cy * gb;
+    const bool hi = (lane & 8) != 0;
+    double a = hi ? gb : ga, bx = hi ? xb : xa, by = hi ? yb : ya;            // kept
+    a += __shfl_xor_sync(kAll, hi ? ga : gb, 8);                                // the partner's
+    bx += __shfl_xor_sync(kAll, hi ? xa : xb, 8);
+    by += __shfl_xor_sync(kAll, hi ? ya : yb, 8);
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1) {
+        a += __shfl_xor_sync(kAll, a, o);
+        bx += __shfl_xor_sync(kAll, bx, o);
+        by += __shfl_xor_sync(kAll, by, o);
+    }
+    const double ir = recip(a);
+    const double u = bx * ir, v = by * ir;
+    const int base = lane & 16;
+    u0 = __shfl_sync(kAll, u, base);
+    v0 = __shfl_sync(kAll, v, base);
+    u1 = __shfl_sync(kAll, u, base + 8);
+    v1 = __shfl_sync(kAll, v, base + 8);
+}
+
 // Sliding y-window per thread: last value, face difference and oriented slope of
 // each y-moving population (float32: per population pair).
 template <typename R> struct Win;
@@ -356,6 +388,7 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
               int *err)
 {
     using S = StreamShape<R>;
+    static_assert(sizeof(R) == sizeof(float) || !Dev, "float64 stores f itself (halo_velocity2 takes rho = sum f)");
     constexpr int BW = S::BW;
     extern __shared__ __align__(128) unsigned char smraw[];
     R *ring = reinterpret_cast<R *>(smraw);
@@ -459,6 +492,7 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
         release(kb + 1, pb.slot);
         Pos p0 = pc, p1 = pd, p2 = pd;   // rows y, y+1, y+2
         p2.next();
+        [[maybe_unused]] R uh_next = R(0), vh_next = R(0);   // float64: halo of row y+1, from the pair
 #pragma unroll 1
         for (int i = 0; i < len; i++) {
             if (!(ok = wait(p2))) break;
@@ -470,7 +504,16 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
             else
                 moments_at<Dev>(C, colp(r1), c1, u_p, v_p, ir_p);
             R uh, vh;
-            halo_velocity<R, Dev>(C, r0 + hoff, cxl, cyl, uh, vh);
+            if constexpr (sizeof(R) == sizeof(double)) {
+                if ((i & 1) == 0) {
+                    halo_velocity2(r0 + hoff, r1 + hoff, cxl, cyl, lane, uh, vh, uh_next, vh_next);
+                } else {
+                    uh = uh_next;
+                    vh = vh_next;
+                }
+            } else {
+                halo_velocity<R, Dev>(C, r0 + hoff, cxl, cyl, uh, vh);
+            }
             R uxm = __shfl_up_sync(0xffffffffu, u_0, 1), uxp = __shfl_down_sync(0xffffffffu, u_0, 1);
             R vxm = __shfl_up_sync(0xffffffffu, v_0, 1), vxp = __shfl_down_sync(0xffffffffu, v_0, 1);
             if (lane == 0) { uxm = uh; vxm = vh; }
