@@ -40,7 +40,7 @@ BYTES_PER_CELL = {"f32": 128, "f64": 256}     # read 16 populations + write 16 p
 # Algorithmic float64 operations per cell-update of the symmetry-factored step
 # (each add, multiply, FMA or division = one float64-pipe operation; the limiter's
 # magnitude comparisons and sign logic are exact integer operations and not counted).
-FP64_OPS_PER_CELL = 337
+FP64_OPS_PER_CELL = 335
 TOTALS_EVERY = 100
 # DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture of the
 # current kernels (profiles/k_step_tma_*_shear_layer.md: 4096^2 FP32, 2048^2 FP64, scaled by

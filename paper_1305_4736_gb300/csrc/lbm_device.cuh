@@ -226,11 +226,12 @@ __host__ __device__ __forceinline__ Moments<R> moments_of(const Shells<R> &s)
 // Inputs: drho = rho - rho0, j, dP = P - P0 (u0 = 0).  Output: f_hat^eq - f_hat^eq0,
 // all 16 rows.  With rho0 = P0 = T0 = e0 = 0 this is f_hat^eq itself.
 // ---------------------------------------------------------------------------
+// ux, uy: the flow velocity j / rho (jx * ir, jy * ir), passed in where the caller has it.
 template <typename R, bool Dev>
-__host__ __device__ __forceinline__ void feq_hat_dev(const Coef<R> &C, R drho, R jx, R jy, R dP, R ir, R *q)
+__host__ __device__ __forceinline__ void feq_hat_dev(const Coef<R> &C, R drho, R jx, R jy, R ux, R uy, R dP, R ir,
+                                                    R *q)
 {
     const R b = C.b;
-    const R ux = jx * ir, uy = jy * ir;
     const R jx2 = jx * ux, jy2 = jy * uy, J2 = jx2 + jy2;
     const R Pt = Dev ? C.P0 + dP : dP;                   // total pressure
     const R e_dev = b * dP + J2;                          // e - e0
@@ -251,14 +252,23 @@ __host__ __device__ __forceinline__ void feq_hat_dev(const Coef<R> &C, R drho, R
     q[10] = g4 * uy;
     q[11] = (R(2.0) * Pt + dxy) * ux;
     q[12] = (dxy - R(2.0) * Pt) * uy;
-    const R T = Pt * ir;
-    R iso;
-    if (Dev) iso = ir * (dP * (Pt + C.P0) - C.P0T0 * drho);   // P^2/rho - P0^2/rho0
-    else     iso = Pt * T;                                     // P^2 / rho
-    q[13] = C.two_b2 * iso + C.six_b * T * J2 + J2 * J2 * ir;
+    // row 14: 2(b+2) P^2/rho + (6+b) P J2/rho + J2^2/rho
+    if (Dev) {
+        const R T = Pt * ir;
+        const R iso = ir * (dP * (Pt + C.P0) - C.P0T0 * drho);   // P^2/rho - P0^2/rho0
+        q[13] = C.two_b2 * iso + C.six_b * T * J2 + J2 * J2 * ir;
+    } else {
+        q[13] = ir * (Pt * (C.two_b2 * Pt + C.six_b * J2) + J2 * J2);
+    }
     const R k = C.b4 * Pt + J2;
     q[14] = k * ux * uy;
     q[15] = k * dxy * ir;
+}
+
+template <typename R, bool Dev>
+__host__ __device__ __forceinline__ void feq_hat_dev(const Coef<R> &C, R drho, R jx, R jy, R dP, R ir, R *q)
+{
+    feq_hat_dev<R, Dev>(C, drho, jx, jy, jx * ir, jy * ir, dP, ir, q);
 }
 
 // Populations from a full moment vector q (16 rows) with the full inverse blocks.
@@ -373,17 +383,17 @@ __device__ __forceinline__ R flux_diff(R fmm, R fm, R f0, R fp, R hh)
 // Collision (Eq. 3 with the energy-flux correction of Sec. II):
 //   out = dt M^-1 S (f_hat - f_hat^eq), residuals of rows 1..4 are zero.
 // ---------------------------------------------------------------------------
+// ux, uy: j / rho as jx * ir, jy * ir (the caller's, bit for bit).
 template <typename R, bool Dev>
 __device__ __forceinline__ void collide(const Params &P, const Shells<R> &sh, R drho, R jx, R jy, R de,
-                                        R ir, R dxux, R dyux, R dxuy, R dyuy, R *out)
+                                        R ir, R ux, R uy, R dxux, R dyux, R dxuy, R dyuy, R *out)
 {
     const Coef<R> &C = coef<R>(P);
     const Moments<R> M = moments_of(sh);
-    const R ux = jx * ir, uy = jy * ir;
     const R J2 = jx * ux + jy * uy;
     const R dP = (de - J2) * C.inv_b;
     R q[NQ];
-    feq_hat_dev<R, Dev>(C, drho, jx, jy, dP, ir, q);
+    feq_hat_dev<R, Dev>(C, drho, jx, jy, ux, uy, dP, ir, q);
     R D[NQ];
     D[4] = (de - R(kEta2) * sh.S[0]) - q[4];   // row 5 from the caller's e (equal to M.m[3])
 #pragma unroll

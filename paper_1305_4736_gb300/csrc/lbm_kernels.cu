@@ -134,7 +134,7 @@ __device__ __forceinline__ void step_tile(const Params &P, const R *__restrict__
         const R dyuy = sv[k + W] - sv[k - W];
 
         R acc[NQ];
-        collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+        collide<R, Dev>(P, sh, drho, jx, jy, de, ir, jx * ir, jy * ir, dxux, dyux, dxuy, dyuy, acc);
 #pragma unroll
         for (int q = 0; q < NQ; q++) acc[q] = f[q] - acc[q];
 

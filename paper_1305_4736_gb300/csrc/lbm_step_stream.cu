@@ -537,8 +537,8 @@ k_step_stream(const __grid_constant__ Params P, const __grid_constant__ CUtensor
 #pragma unroll
                 for (int q = 0; q < NQ; q++) f[q] = s0[q * BW];
                 double acc[NQ];
-                collide<double, Dev>(P, c0.sh, c0.drho, c0.jx, c0.jy, c0.de, ir_0, uxp - uxm, u_p - u_m, vxp - vxm,
-                                     v_p - v_m, acc);
+                collide<double, Dev>(P, c0.sh, c0.drho, c0.jx, c0.jy, c0.de, ir_0, u_0, v_0, uxp - uxm, u_p - u_m,
+                                     vxp - vxm, v_p - v_m, acc);
                 if (Lim == 0) xedge_row(xe, r0);
                 convect_store<Lim>(C, W, f, acc, s0, colp(r1), colp(r2), gx < nx, fout, P.plane, cg, xe, lane);
                 c0 = c1;

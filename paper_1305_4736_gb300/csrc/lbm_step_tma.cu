@@ -276,7 +276,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
             const R dxuy = sv[ui + 1] - sv[ui - 1];
             const R dyuy = sv[ui + S::UW] - sv[ui - S::UW];
             R acc[NQ];
-            collide<R, Dev>(P, sh, drho, jx, jy, de, ir, dxux, dyux, dxuy, dyuy, acc);
+            collide<R, Dev>(P, sh, drho, jx, jy, de, ir, jx * ir, jy * ir, dxux, dyux, dxuy, dyuy, acc);
             const bool store = gx < nx && gy < ny;
             const long long cg = (long long)(gy + OY) * P.pitch + (gx + OX);
 #pragma unroll
