@@ -13,7 +13,8 @@
 // per step:
 //   - flow velocity of the next row at its own column (u(y+1), kept in
 //     registers with u(y) and u(y-1)) and of the two columns left and right of
-//     the warp in row y (a 16-lane reduction), for the gradient of u;
+//     the warp in row y (a 16-lane reduction; float64 reduces rows y and y+1
+//     together every other row), for the gradient of u;
 //   - MRT collision with the energy-flux correction (Eq. 3, Sec. II);
 //   - limited x convection from the staged row; limited y convection from a
 //     sliding window per thread that lives for the whole range (each slope
