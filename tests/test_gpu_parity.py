@@ -366,3 +366,24 @@ def test_tma_kernel_parity_with_oracle(orc, lbm):
     O.init(*p.fields())
     O.step(300)
     _assert_fp64(fp64_errors(s, O))
+
+
+# ------------------------------------------------------------------ 1000 steps, reduced C3 / C4
+@pytest.mark.parametrize("name", ["shock_interface_512x128", "shear_layer_1024x1024"])
+def test_reduced_configs_1000_steps_every_fp64_kernel(orc, lbm, name):
+    """The shock-interface and shear-layer configurations reduced to 512 x 128 and 1024 x 1024
+    (same physics), 1000 steps: the automatic float64 kernel, the streaming kernel and the
+    TMA-staged tile kernel each match one oracle run to 1e-10 on rho, u, T."""
+    p = (wl.shock_interface(nx=512, ny=128, steps=1000) if name.startswith("shock")
+         else wl.shear_layer(1024, steps=1000))
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc)
+    O.init(*p.fields())
+    O.step(1000)
+    for kernel in (0, 5, 2):
+        s = lbm.Solver.from_problem(p, step_kernel=kernel)
+        s.init(*p.fields())
+        s.step(1000)
+        errs = fp64_errors(s, O)
+        s.close()
+        for k, v in errs.items():
+            assert v <= TOL, f"kernel {kernel}, {k}: {v:.3e} ({errs})"
