@@ -222,6 +222,14 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out);
 int lbm_batch_step(lbm_batch *batch, int n);        /* asynchronous on the shared stream */
 void lbm_batch_destroy(lbm_batch *batch);           /* waits for the stream; NULL-safe */
 
+/* Failure-path check of the bounded device waits of the TMA-fed step kernels, with no GPU
+   fault: one warp waits on an mbarrier phase that nothing completes, using the kernels' own
+   bounded wait (global-timer limit 2 s); the wait gives up, the kernel records it and returns,
+   and the device stays usable.  Returns LBM_ERR_TIMEOUT when the wait ran out (the expected
+   outcome), LBM_OK if the phase completed, LBM_ERR_CUDA on a CUDA error.  *elapsed_ms (may be
+   NULL) receives the kernel's duration.  Not part of the paper's method. */
+int lbm_wait_selftest(int device, double *elapsed_ms);
+
 /* Largest ny accepted by lbm_totals_noalloc (its scratch holds one partial per grid row). */
 #define LBM_TOTALS_NOALLOC_MAX_ROWS 16384
 

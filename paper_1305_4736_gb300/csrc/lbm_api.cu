@@ -881,6 +881,24 @@ int lbm_peak_fp64(int device, double *flops)
     return LBM_OK;
 }
 
+int lbm_wait_selftest(int device, double *elapsed_ms)
+{
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaSetDevice");
+    int *flag = nullptr;
+    ce = cudaMalloc(&flag, sizeof(int));
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "cudaMalloc");
+    float ms = 0.f;
+    int timed_out = 0;
+    ce = lbm::wait_selftest(flag, &ms);
+    if (ce == cudaSuccess) ce = cudaMemcpy(&timed_out, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "wait self-test");
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (timed_out) return fail(nullptr, LBM_ERR_TIMEOUT, "the bounded wait ran out (expected)");
+    return LBM_OK;
+}
+
 int lbm_autotune(lbm_ctx *c, int reps, int *choice)
 {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");

@@ -76,6 +76,9 @@ struct TmaShape {
     static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * (sizeof(R) == sizeof(float) ? 2 : 3) * UW * UH;
 };
 bool tma_supported(const Params &P, int prec);
+// Failure-path check of the bounded mbarrier waits (lbm_wait_selftest): *flag = 1 when the
+// wait on a phase that nothing completes gave up at its limit; *ms = the kernel's duration.
+cudaError_t wait_selftest(int *flag, float *ms);
 cudaError_t tma_prepare();   // opt the kernels in to their dynamic shared memory (once per device)
 // `tmap` points to the CUtensorMap of the input buffer fin (3-D: pitch x (ny+4) x 16).  Tiles at a
 // periodic x edge take their x halo from the wrapped interior of fin, so on a grid periodic in x

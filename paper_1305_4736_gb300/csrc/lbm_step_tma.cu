@@ -450,6 +450,41 @@ cudaError_t tma_pipe_prepare()
 }
 
 // ---------------------------------------------------------------------------
+// Failure path of the bounded copy waits: one warp waits on an mbarrier phase that nothing
+// completes (no copy is issued, no thread arrives).  mbar_wait gives up at its global-timer
+// limit; the kernel records that in *flag and returns, leaving no copy in flight.
+__global__ void k_wait_selftest(int *flag)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(bar_a, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+cudaError_t wait_selftest(int *flag, float *ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaMemset(flag, 0, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0);
+    if (ce == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(flag);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return ce;
+}
+
 bool tma_supported(const Params &P, int prec)
 {
     const int sh = prec == 0 ? TmaShape<double>::SH : TmaShape<float>::SH;

@@ -31,7 +31,7 @@ LBM_FP64, LBM_FP32_DEV = 0, 1
 EXPORTS = ["lbm_create", "lbm_create_ex", "lbm_init", "lbm_step", "lbm_moments", "lbm_moments_central",
            "lbm_totals", "lbm_get_state", "lbm_get_state_rows", "lbm_set_state", "lbm_step_count", "lbm_step_kernel",
            "lbm_footprint", "lbm_profile_begin", "lbm_profile_end", "lbm_peak_fp64", "lbm_totals_noalloc",
-           "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy",
+           "lbm_autotune", "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_wait_selftest",
            "lbm_last_error", "lbm_destroy"]
 
 
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.lbm_profile_begin.argtypes = [vp, ctypes.c_int]
         lib.lbm_profile_end.argtypes = [vp, _D]
         lib.lbm_peak_fp64.argtypes = [ctypes.c_int, _D]
+        lib.lbm_wait_selftest.argtypes = [ctypes.c_int, _D]
+        lib.lbm_wait_selftest.restype = ctypes.c_int
         lib.lbm_totals_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_void_p, _D]
         lib.lbm_totals_noalloc.restype = ctypes.c_int
@@ -209,6 +211,14 @@ def lbm_peak_fp64(device=0) -> float:
     out = np.zeros(1)
     _check(load().lbm_peak_fp64(int(device), _p(out)))
     return float(out[0])
+
+
+def lbm_wait_selftest(device=0):
+    """Failure-path check of the kernels' bounded waits: (status, kernel ms); the expected
+    status is LBM_ERR_TIMEOUT."""
+    out = np.zeros(1)
+    rc = load().lbm_wait_selftest(int(device), _p(out))
+    return int(rc), float(out[0])
 
 
 def lbm_totals_noalloc(f_device_ptr, nx, ny, dx, stream=None):

@@ -184,3 +184,19 @@ def test_tma_kernel_across_set_state_and_batch_steps(lbm):
     ref.close()
     assert np.isfinite(got).all()
     assert np.abs(got - want).max() <= ROUNDOFF[1] * np.abs(want).max()
+
+
+def test_bounded_wait_runs_out_without_a_fault(lbm):
+    """A wait on an mbarrier phase that nothing completes (the kernels' own bounded wait) gives
+    up at its 2 s limit: the kernel records it, the host reads LBM_ERR_TIMEOUT, and the device
+    stays usable for the next solve."""
+    rc, ms = lbm.lbm_wait_selftest(0)
+    assert rc == lbm.LBM_ERR_TIMEOUT
+    assert 1800.0 <= ms <= 10000.0
+    p = wl.shear_layer(256, seed=2, steps=5)
+    s = lbm.Solver.from_problem(p, precision=1)
+    s.init(*p.fields())
+    s.step(5)
+    rho = s.moments()[0]
+    s.close()
+    assert np.isfinite(rho).all()
