@@ -137,7 +137,9 @@ __device__ __noinline__ void wrap_halo(const Params &P, const R *__restrict__ fi
     }
 }
 
-template <typename R, bool Dev, int Lim>
+// Wrap: the grid's x halo is wrapped in the kernel (P.wrap bit 0); a separate instantiation,
+// so that the other grids run a kernel without that branch.
+template <typename R, bool Dev, int Lim, bool Wrap>
 __global__ void __launch_bounds__(kTmaTX * TmaShape<R>::TT, TmaShape<R>::CTAS)
 k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm, const R *__restrict__ fin,
            R *__restrict__ fout, int *err)
@@ -192,7 +194,7 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         return;
     }
     // tiles whose staged box reaches past a periodic x edge (uniform per CTA)
-    if ((P.wrap & 1) && (x0 < S::HX || x0 + kTmaTX + S::HX > nx)) {
+    if (Wrap && (x0 < S::HX || x0 + kTmaTX + S::HX > nx)) {
         wrap_halo<R>(P, fin, tile, x0, y0, tid, kTmaTX * S::TT);
         __syncthreads();
     }
@@ -491,28 +493,32 @@ bool tma_supported(const Params &P, int prec)
     return P.pitch >= TmaShape<float>::SW && P.ny + 4 >= sh && P.nx >= kTmaTX;
 }
 
+template <typename R, bool Dev, bool Wrap>
+static void launch_tma_lim(const Params &P, const CUtensorMap &tm, const R *a, R *b, int *err, cudaStream_t st)
+{
+    using S = TmaShape<R>;
+    const dim3 block(kTmaTX, S::TT);
+    const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
+    if (P.limiter == 0) k_step_tma<R, Dev, 0, Wrap><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+    else if (P.limiter == 1) k_step_tma<R, Dev, 1, Wrap><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+    else k_step_tma<R, Dev, 2, Wrap><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+}
+
 cudaError_t launch_step_tma(const Params &P, int prec, const void *tmap, const void *fin, void *fout, int *err,
                             cudaStream_t st)
 {
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
+    const bool wrap = (P.wrap & 1) != 0;
     if (prec == 0) {
-        using S = TmaShape<double>;
-        const dim3 block(kTmaTX, S::TT);
-        const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
         const double *a = (const double *)fin;
         double *b = (double *)fout;
-        if (P.limiter == 0) k_step_tma<double, false, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
-        else if (P.limiter == 1) k_step_tma<double, false, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
-        else k_step_tma<double, false, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        if (wrap) launch_tma_lim<double, false, true>(P, tm, a, b, err, st);
+        else launch_tma_lim<double, false, false>(P, tm, a, b, err, st);
     } else {
-        using S = TmaShape<float>;
-        const dim3 block(kTmaTX, S::TT);
-        const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
         const float *a = (const float *)fin;
         float *b = (float *)fout;
-        if (P.limiter == 0) k_step_tma<float, true, 0><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
-        else if (P.limiter == 1) k_step_tma<float, true, 1><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
-        else k_step_tma<float, true, 2><<<grid, block, S::smem_bytes, st>>>(P, tm, a, b, err);
+        if (wrap) launch_tma_lim<float, true, true>(P, tm, a, b, err, st);
+        else launch_tma_lim<float, true, false>(P, tm, a, b, err, st);
     }
     return cudaGetLastError();
 }
@@ -523,12 +529,18 @@ cudaError_t tma_prepare()
     auto set = [&](const void *fn, size_t bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set((const void *)k_step_tma<double, false, 0>, TmaShape<double>::smem_bytes);
-    set((const void *)k_step_tma<double, false, 1>, TmaShape<double>::smem_bytes);
-    set((const void *)k_step_tma<double, false, 2>, TmaShape<double>::smem_bytes);
-    set((const void *)k_step_tma<float, true, 0>, TmaShape<float>::smem_bytes);
-    set((const void *)k_step_tma<float, true, 1>, TmaShape<float>::smem_bytes);
-    set((const void *)k_step_tma<float, true, 2>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 0, false>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 1, false>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 2, false>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 0, true>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 1, true>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<double, false, 2, true>, TmaShape<double>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 0, false>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 1, false>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 2, false>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 0, true>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 1, true>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma<float, true, 2, true>, TmaShape<float>::smem_bytes);
     return e;
 }
 
