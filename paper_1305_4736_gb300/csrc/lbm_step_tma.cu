@@ -104,7 +104,7 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
             if (sy > 0) out = fma2(ld2(&C.ncry[sa]), tyv, out);
             if (sy < 0) out = fma2(ld2(&C.cry[sa]), tyv, out);
             if (sx != 0) out = fma2(ld2(&C.ncr[sa]), tx, out);
-            if (store) out2[pr * P.plane + cg] = out;
+            if (store) __stcs(out2 + pr * P.plane + cg, out);   // evict-first: not re-read before it leaves L2
         }
     }
 }
