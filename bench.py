@@ -45,7 +45,7 @@ TOTALS_EVERY = 100
 # DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture of the
 # current kernels (profiles/k_step_tma_*_shear_layer.md: 4096^2 FP32, 2048^2 FP64, scaled by
 # the cell count); None once the kernel changes and until it is captured again.
-TRAFFIC_PER_CELL = {"f32": 126.13, "f64": 251.43}   # dram bytes per cell, ncu captures in profiles/
+TRAFFIC_PER_CELL = {"f32": 125.87, "f64": 251.43}   # dram bytes per cell, ncu captures in profiles/
 
 
 def parse_args(argv=None):
