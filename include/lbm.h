@@ -123,7 +123,10 @@ typedef struct lbm_ctx lbm_ctx;   /* opaque, owned by the library */
    Isotropy s_5 = s_6 = s_7 and s_8 = s_9 is required (Sec. II).
    Errors: LBM_ERR_ARG, LBM_ERR_CFL (6 dt > min(dx, dy): a Courant number above 1),
    LBM_ERR_STABILITY, LBM_ERR_OOM, LBM_ERR_CUDA.
-   On success *out receives the context (FP64, legacy default stream, cudaMalloc). */
+   On success *out receives the context (FP64, legacy default stream).  Its device memory
+   comes from cudaMalloc: with no allocator given, the library falls back to cudaMalloc /
+   cudaFree.  Callers that keep device memory in a framework's pool (the Python binding
+   passes PyTorch's caching allocator) use lbm_create_ex with lbm_options.allocator. */
 int lbm_create(int nx, int ny, double dx, double dt, double gamma, double Pr,
                const double s[16], int limiter, const lbm_bc *bc, lbm_ctx **out);
 
@@ -239,18 +242,21 @@ int lbm_wait_selftest(int device, double *elapsed_ms);
    caching pool, a serving engine with a fixed memory plan), or they must not call
    cudaMalloc / cudaFree, which can synchronise the whole device.
    f: device pointer to caller-owned float64 populations, dense [16][ny][nx] (the
-   layout lbm_get_state writes), on the current device.  out: host array that
-   receives sum rho, sum j_x, sum j_y, sum e, each times dx dx (as lbm_totals).
+   layout lbm_get_state writes), on the current device.  dx, dy: grid spacings.
+   out: host array that receives sum rho, sum j_x, sum j_y, sum e, each times the
+   cell area dx dy (the scaling of lbm_totals).
    stream: cudaStream_t (NULL = legacy default stream); the call waits for it.
    Scratch: a fixed file-scope device array of (LBM_TOTALS_NOALLOC_MAX_ROWS + 1) x 4
    doubles (512 KB), held by every GPU that loads the library until the process
    exits.  The first call on a device looks up that array's address on the device
-   (make it before any stream capture).  All calls share the array; each overwrites
-   what it uses, so nothing needs clearing, but calls that overlap on the GPU race
-   on it and must be serialised by the caller.
-   Errors: LBM_ERR_ARG (NULL pointer, nx or ny < 1, dx <= 0, ny above
+   and keeps it (make that first call before any stream capture); after a
+   cudaDeviceReset of the device the kept address is stale, so do not call this on a
+   device that was reset.  All calls share the array; each overwrites what it uses,
+   so nothing needs clearing, but calls that overlap on the GPU race on it and must
+   be serialised by the caller.
+   Errors: LBM_ERR_ARG (NULL pointer, nx or ny < 1, dx or dy <= 0, ny above
    LBM_TOTALS_NOALLOC_MAX_ROWS), LBM_ERR_CUDA.  No cudaMalloc or cudaFree is called. */
-int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream, double out[4]);
+int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, double dy, void *stream, double out[4]);
 
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);

@@ -1,4 +1,4 @@
-"""Build liblbm.so in-tree for sm_103a (nvcc, two translation units in parallel).
+"""Build liblbm.so in-tree for sm_103a (nvcc, one process per translation unit, in parallel).
 
 The library links the CUDA runtime statically, so it loads on a machine without
 a GPU driver (its entry points then return LBM_ERR_CUDA).

@@ -9,7 +9,9 @@
 //
 // The first call on a device looks up the array's device address on that
 // device (cudaGetSymbolAddress, with the device current); make that first call
-// before any stream capture.  All calls share the array and each call
+// before any stream capture.  The address is kept for the life of the process:
+// after a cudaDeviceReset of that device it is no longer valid, so the entry
+// point must not be called on a device that was reset.  All calls share the array and each call
 // overwrites the rows it uses and the result slot, so nothing needs clearing;
 // calls whose work overlaps on the GPU (different streams, or different host
 // threads on one device) race on it and must be serialised by the caller.
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(const double *__restrict__ f,
     }
 }
 
-// One block: the row partials in a fixed order, times dx^2, into the result slot.
+// One block: the row partials in a fixed order, times the cell area dx dy, into the result slot.
 __global__ void __launch_bounds__(kThreads) k_final(int ny, double scale, double *scratch)
 {
     __shared__ double red[kThreads / 32];
@@ -89,10 +91,11 @@ __global__ void __launch_bounds__(kThreads) k_final(int ny, double scale, double
 
 }  // namespace
 
-extern "C" int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, void *stream, double out[4])
+extern "C" int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, double dy, void *stream,
+                                  double out[4])
 {
     if (!f || !out) return LBM_ERR_ARG;
-    if (nx < 1 || ny < 1 || !(dx > 0.0)) return LBM_ERR_ARG;
+    if (nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0)) return LBM_ERR_ARG;
     if (ny > kRows) return LBM_ERR_ARG;   // the row partials are sized for LBM_TOTALS_NOALLOC_MAX_ROWS rows
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
@@ -109,7 +112,7 @@ extern "C" int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, vo
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int grid = ny < 1024 ? ny : 1024;
     k_rows<<<grid, kThreads, 0, st>>>(f, nx, ny, scratch);
-    k_final<<<1, kThreads, 0, st>>>(ny, dx * dx, scratch);
+    k_final<<<1, kThreads, 0, st>>>(ny, dx * dy, scratch);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaMemcpyAsync(out, scratch + 4 * kRows, 4 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return LBM_ERR_CUDA;

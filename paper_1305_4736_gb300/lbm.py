@@ -96,7 +96,7 @@ def load(path: str = LIB_PATH):
         lib.lbm_wait_selftest.argtypes = [ctypes.c_int, _D]
         lib.lbm_wait_selftest.restype = ctypes.c_int
         lib.lbm_totals_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                           ctypes.c_void_p, _D]
+                                           ctypes.c_double, ctypes.c_void_p, _D]
         lib.lbm_totals_noalloc.restype = ctypes.c_int
         lib.lbm_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.lbm_autotune.restype = ctypes.c_int
@@ -221,11 +221,12 @@ def lbm_wait_selftest(device=0):
     return int(rc), float(out[0])
 
 
-def lbm_totals_noalloc(f_device_ptr, nx, ny, dx, stream=None):
-    """Totals of a dense [16][ny][nx] float64 device field, without device allocation."""
+def lbm_totals_noalloc(f_device_ptr, nx, ny, dx, dy=None, stream=None):
+    """Totals of a dense [16][ny][nx] float64 device field (times dx dy), without device allocation."""
     out = np.zeros(4)
     _check(load().lbm_totals_noalloc(ctypes.c_void_p(int(f_device_ptr)), int(nx), int(ny), float(dx),
-                                     ctypes.c_void_p(int(stream or 0)), _p(out)))
+                                     float(dx if dy is None else dy), ctypes.c_void_p(int(stream or 0)),
+                                     _p(out)))
     return out
 
 
