@@ -3,13 +3,24 @@
 
 Workload: the 8192 x 8192 doubly periodic low-Mach shear layer (rho = T = 1,
 u = +-0.05 tanh layers, seeded v perturbation; gamma = 1.4, Pr = 0.71,
-dt = 1e-5), the largest grid of the benchmark set.  A step is one pass of the
+dt = 5.09e-6, a largest Courant number of 1/4), the largest grid of the benchmark set.  A step is one pass of the
 hot path: ghost fill + fused collide/convect kernel; the float64 totals
 reduction (rho, j, e) runs every 100 steps and once at the end.
 
 The headline line is the FP32 deviation mode (f stored as f - f^eq0 in float32,
 bound by HBM: 128 algorithmic bytes per cell-update); the FP64 mode (bound by the
-float64 pipe) is measured in the same run and reported under "fp64".
+float64 pipe) is measured in the same run and reported under "fp64".  The same
+line carries:
+  configs    every configuration of the benchmark set: the Sod tube 200x4 (a full
+             2000-step solve), thermal Couette 4x200 at Pr 0.5, 1, 2, the
+             shock-interface 4096x1024 in FP64 and FP32 with rooflines, and the
+             oracle on all host cores and on one thread for each;
+  precision  FP32 against FP64 at each stated length: the shear layer after 2000
+             steps (whole field, totals drift) and the shock-interface over 5000
+             steps (rho, u, T every 100 steps, Delta every 500);
+  batch      24 uneven grids stepped as one batch;
+  serving    the 512-request mixed stream (grids up to 2048x512, 1000 steps each),
+             with FP64-only batched serving against one-at-a-time FP64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -42,10 +53,35 @@ BYTES_PER_CELL = {"f32": 128, "f64": 256}     # read 16 populations + write 16 p
 # magnitude comparisons and sign logic are exact integer operations and not counted).
 FP64_OPS_PER_CELL = 335
 TOTALS_EVERY = 100
-# DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture of the
-# current kernels (profiles/k_step_tma_*_shear_layer.md: 4096^2 FP32, 2048^2 FP64, scaled by
-# the cell count); None once the kernel changes and until it is captured again.
-TRAFFIC_PER_CELL = {"f32": 125.87, "f64": 251.43}   # dram bytes per cell, ncu captures in profiles/
+# DRAM bytes (read + write) per cell of one fused-step launch from an ncu capture (profiles/:
+# 4096^2 FP32, 2048^2 FP64, scaled by the cell count), each with the SHA-256 (first 16 hex digits)
+# of the kernel sources it was captured from.  bench reports the traffic only while the sources
+# still hash to that value, else null.
+TRAFFIC_PER_CELL = {
+    "f32": {"bytes": 125.87, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "4d6d8aaddb3ad2e2"},
+    "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "1fae702a20fe4afb"},
+}
+
+
+def kernel_sources_sha(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1305_4736_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(mode: str, cells: int, kernel: str):
+    """ncu DRAM bytes of one fused-step launch scaled to `cells`, or None when the captured
+    kernel is not the one that ran or its sources changed since the capture."""
+    t = TRAFFIC_PER_CELL.get(mode)
+    want = "k_step_tma<" if mode == "f32" else "k_step_stream<"
+    if not t or not kernel.startswith(want) or kernel_sources_sha(t["sources"]) != t["sha"]:
+        return None
+    return t["bytes"] * cells
 
 
 def parse_args(argv=None):
@@ -61,9 +97,13 @@ def parse_args(argv=None):
     ap.add_argument("--step-kernel", type=int, default=0,
                     help="lbm_options.step_kernel (0 = automatic, 1/3/4/7 plain, 2 TMA tiles, 5 streaming, "
                          "6 double-buffered TMA tiles)")
-    ap.add_argument("--serving-requests", type=int, default=64,
+    ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving measurement (0 = skip)")
-    ap.add_argument("--serving-steps", type=int, default=200)
+    ap.add_argument("--serving-steps", type=int, default=1000)
+    ap.add_argument("--serving-max-grid", type=int, nargs=2, default=(2048, 512), metavar=("NX", "NY"))
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration measurements")
+    ap.add_argument("--no-precision-study", action="store_true",
+                    help="skip the FP32-vs-FP64 runs at each configuration's stated length")
     return ap.parse_args(argv)
 
 
@@ -245,28 +285,6 @@ def totals_drift(t0, t1, steps):
             "energy": abs(float(t1[3]) - float(t0[3])) / e}
 
 
-def precision_compare(lbm, p, device, steps=20):
-    """FP32 deviation mode against FP64 on the same fields after `steps` steps: L1 and max
-    relative errors of rho, u (as a vector) and T over the whole grid."""
-    import numpy as np
-    out = {}
-    for prec in (lbm.LBM_FP64, lbm.LBM_FP32_DEV):
-        s = lbm.Solver.from_problem(p, precision=prec, device=device)
-        s.init(*p.fields())
-        s.step(steps)
-        out[prec] = s.moments()
-        s.close()
-    a, b = out[lbm.LBM_FP32_DEV], out[lbm.LBM_FP64]
-
-    def rel(x, y):
-        return {"l1": float(np.abs(x - y).sum() / np.abs(y).sum()), "max": float(np.abs(x - y).max() / np.abs(y).max())}
-    du = np.maximum(np.abs(a[1] - b[1]), np.abs(a[2] - b[2]))
-    umax = max(np.abs(b[1]).max(), np.abs(b[2]).max())
-    usum = (np.abs(b[1]) + np.abs(b[2])).sum()
-    return {"steps": steps, "rho": rel(a[0], b[0]), "T": rel(a[3], b[3]),
-            "u": {"l1": float(du.sum() / usum), "max": float(du.max() / umax)}}
-
-
 def cpu_baseline_run(p_full, crop: int, steps_budget_s: float = 12.0, max_steps: int = 400):
     """The CPU oracle, as it stands, on a crop of the workload (all host cores)."""
     import numpy as np
@@ -332,7 +350,7 @@ def gpu_arm(args):
                    "totals_every": TOTALS_EVERY, "l2": "inputs larger than L2 (4.3 GB per population buffer)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                     "traffic": (TRAFFIC_PER_CELL["f32"] * cells if TRAFFIC_PER_CELL.get("f32") else None),
+                     "traffic": traffic_per_launch("f32", cells, r32["kernel"]),
                      "kernel": r32["kernel"],
                      "kernel_ms": r32["step_kernel_ms"], "algorithmic_bytes_per_launch": BYTES_PER_CELL["f32"] * cells,
                      "peak_source": f"{peak_src} hbm_gbs"},
@@ -347,14 +365,12 @@ def gpu_arm(args):
     }
     if args.mode == "both":
         line["fp64"] = fp64_line(lbm, p, args, device, world, hbm)
-        if rank == 0:
-            line["precision"] = precision_compare(lbm, p, device)
     finish(line, p, args, rank, world)
 
 
 def fp64_line(lbm, p, args, device, world, hbm):
     cells = p.nx * p.ny
-    k64 = max(3, args.steps // 10) if args.mode == "both" else args.steps
+    k64 = max(20, args.steps // 10) if args.mode == "both" else args.steps
     peak64 = lbm.lbm_peak_fp64(device)
     with ClockSampler(device) as clk64:
         r64 = run_mode(lbm, p, lbm.LBM_FP64, k64, args.warmup, device, world, args.step_kernel)
@@ -368,7 +384,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
                    "grid": [p.nx, p.ny], "l2": "inputs larger than L2 (8.6 GB per population buffer)"},
         "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T fp64-op/s", "frac": ops / peak_ops,
-                     "traffic": (TRAFFIC_PER_CELL["f64"] * cells if TRAFFIC_PER_CELL.get("f64") else None),
+                     "traffic": traffic_per_launch("f64", cells, r64["kernel"]),
                      "kernel": r64["kernel"], "kernel_ms": r64["step_kernel_ms"],
                      "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
                      "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
@@ -382,25 +398,46 @@ def fp64_line(lbm, p, args, device, world, hbm):
 
 
 def serving_measure(count, steps, max_nx, max_ny, device, seed=1305):
-    """Continuous-batching serving of a seeded mixed request stream (Riemann, Couette,
-    shock-interface; FP32/FP64 50/50) against one-at-a-time FP64 solving of the same
-    requests.  Arrivals are Poisson at 1.5x the measured one-at-a-time FP64 rate."""
+    """Continuous-batching serving of the seeded mixed request stream (Riemann, Couette,
+    shock-interface; FP32/FP64 50/50; grids 64..max_nx x 4..max_ny log-uniform), and the
+    comparison at equal accuracy: the same requests all in FP64, served batched (all available at
+    t = 0) against one at a time.  The mixed stream is also served with Poisson arrivals at 1.5x
+    the one-at-a-time FP64 rate, for time to result (p50/p99 per precision)."""
+    import numpy as np
     from paper_1305_4736_gb300 import serving, workloads as wl
     be = serving.GpuBackend(device)
     reqs = wl.serving_requests(count=count, seed=seed, rate_hz=1.0, max_nx=max_nx, max_ny=max_ny, steps=steps)
-    warm = [dict(r) for r in reqs[:2]]
+    warm = [dict(r) for r in reqs[:3]]
     serving.one_at_a_time(be, warm, precision=0)
+    serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=False).run(warm)
+    t0 = time.perf_counter()
     wall64, _ = serving.one_at_a_time(be, reqs, precision=0)
     rate64 = len(reqs) / wall64
+    all64 = [dict(r, precision=0) for r in reqs]
+    _, cap64 = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=False).run(all64)
+    _, cap = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=False).run(reqs)
     reqs = wl.serving_requests(count=count, seed=seed, rate_hz=1.5 * rate64, max_nx=max_nx, max_ny=max_ny,
                                steps=steps)
     res, st = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=True).run(reqs)
-    _, cap = serving.Engine(be, budget_bytes=64 << 30, chunk=100, realtime=False).run(reqs)
-    return {"capacity_solves_per_s": cap.solves_per_s, "capacity_note": "all requests available at t = 0","requests": count, "steps_per_request": steps, "grids": f"nx 64..{max_nx}, ny 4..{max_ny} log-uniform",
+    per = {}
+    for name, prec in (("fp64", 0), ("fp32", 1)):
+        lat = np.array([r.latency for r in res if r.precision == prec])
+        if lat.size:
+            per[name] = {"solves": int(lat.size), "p50_s": float(np.percentile(lat, 50)),
+                         "p99_s": float(np.percentile(lat, 99))}
+    cells = sum(r["problem"].cells for r in reqs)
+    return {"requests": count, "steps_per_request": steps, "cells_total": cells,
+            "grids": f"nx 64..{max_nx}, ny 4..{max_ny} log-uniform", "precisions": "FP32/FP64 50/50",
+            "fp64_equal_accuracy": {
+                "batched_solves_per_s": cap64.solves_per_s, "one_at_a_time_solves_per_s": rate64,
+                "speedup": cap64.solves_per_s / rate64,
+                "note": "every request in FP64, all available at t = 0; batched = continuous batching "
+                        "through lbm_batch, one at a time = each solve alone on its automatic kernel"},
+            "capacity_mixed_solves_per_s": cap.solves_per_s,
             "arrival_rate_hz": 1.5 * rate64, "solves_per_s": st.solves_per_s, "p50_s": st.p50, "p99_s": st.p99,
-            "wall_s": st.wall, "max_resident_solves": st.max_resident_solves,
+            "per_precision": per, "wall_s": st.wall, "max_resident_solves": st.max_resident_solves,
             "max_resident_gb": st.max_resident_bytes / 1e9, "cell_updates_per_s": st.cell_updates / st.wall,
-            "one_at_a_time_fp64_solves_per_s": rate64, "speedup_vs_one_at_a_time_fp64": st.solves_per_s / rate64}
+            "seconds": time.perf_counter() - t0}
 
 
 def batch_measure(device, steps=20, warmup=3, seed=1305):
@@ -455,13 +492,231 @@ def batch_measure(device, steps=20, warmup=3, seed=1305):
             "one_at_a_time_ms_per_step": ms_solo, "speedup_vs_one_at_a_time": ms_solo / ms}
 
 
+def _pinned_fields(ny, nx, count):
+    import numpy as np
+    return [pinned_like(np.zeros((ny, nx))) for _ in range(count)]
+
+
+def timed_steps(lbm, s, steps, device):
+    """Device time of `steps` steps of one context (CUDA events on its stream) and the mean
+    duration of its fused-step and ghost launches (the library's own events)."""
+    import torch
+    stream = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    lbm.lbm_profile_begin(s.h, steps)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    prof = lbm.lbm_profile_end(s.h)
+    return ev0.elapsed_time(ev1), prof[0] / max(prof[1], 1), prof[2] / max(prof[3], 1)
+
+
+def kernel_name(s, precision):
+    return KERNEL_NAMES[s.step_kernel].format(r="float" if precision else "double",
+                                              d="dev" if precision else "plain")
+
+
+def config_gpu(lbm, p, precision, steps, warmup, device, hbm, peak_ops=None):
+    """Throughput of one configuration in one precision: steps timed on the device after warm-up,
+    with the fused-step kernel's roofline (FP32: HBM bytes; FP64: float64 operations)."""
+    s = lbm.Solver.from_problem(p, precision=precision, device=device)
+    s.init(*p.fields())
+    s.step(warmup)
+    ms, k_ms, g_ms = timed_steps(lbm, s, steps, device)
+    kern = kernel_name(s, precision)
+    s.close()
+    cells = p.nx * p.ny
+    out = {"steps": steps, "ms_per_step": ms / steps, "us_per_step": 1e3 * ms / steps,
+           "cell_updates_per_s": cells * steps / (ms * 1e-3), "kernel": kern,
+           "kernel_ms": k_ms, "ghost_ms": g_ms}
+    if precision:
+        ach = BYTES_PER_CELL["f32"] * cells / (k_ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "peak_source": "measured hbm_gbs"}
+    elif peak_ops:
+        ops = FP64_OPS_PER_CELL * cells / (k_ms * 1e-3)
+        out["roofline"] = {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
+                           "unit": "T fp64-op/s", "frac": ops / peak_ops,
+                           "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64)",
+                           "hbm_frac": BYTES_PER_CELL["f64"] * cells / (k_ms * 1e-3) / 1e9 / hbm}
+    return out
+
+
+def oracle_rate(p, steps, threads, crop=None):
+    """The CPU oracle, as it stands, on problem p (or its leading crop x crop block): cell-updates/s."""
+    import numpy as np
+    from oracle import oracle as orc
+    orc.build()
+    orc.set_threads(threads)
+    nx, ny = (p.nx, p.ny) if crop is None else (min(crop[0], p.nx), min(crop[1], p.ny))
+    fields = [np.ascontiguousarray(a[:ny, :nx]) for a in p.fields()]
+    O = orc.Oracle(nx, ny, p.dx, p.dt, p.gamma, p.s, p.limiter, p.bc, dy=p.dy)
+    O.init(*fields)
+    O.step(1)
+    t0 = time.perf_counter()
+    O.step(steps)
+    el = time.perf_counter() - t0
+    O.close()
+    return {"value": nx * ny * steps / el, "unit": UNIT, "threads": orc.max_threads(),
+            "sample": f"{nx}x{ny}" + ("" if crop is None else f" crop of {p.nx}x{p.ny}") + f", {steps} steps",
+            "seconds": el}
+
+
+def per_config(lbm, device, hbm, peak_ops):
+    """Each configuration of the benchmark set on the GPU (and the oracle on the host):
+    Sod 200x4 (a full 2000-step solve), thermal Couette 4x200 at Pr 0.5, 1, 2 (step time alone and
+    as one batch), the shock-interface 4096x1024 (FP64 and FP32 with rooflines); the 8192^2 shear
+    layer is the headline line itself."""
+    import torch
+    from paper_1305_4736_gb300 import workloads as wl
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    out = {}
+    # Sod: one full solve per precision
+    p = wl.sod(200, 4)
+    sod = {}
+    for name, prec in (("fp64", lbm.LBM_FP64), ("fp32", lbm.LBM_FP32_DEV)):
+        r = config_gpu(lbm, p, prec, p.steps, 200, device, hbm)
+        r["solve_ms"] = r["ms_per_step"] * p.steps
+        r["solves_per_s"] = 1e3 / r["solve_ms"]
+        sod[name] = r
+    sod["oracle"] = {"all_cores": oracle_rate(p, 1000, cores), "one_thread": oracle_rate(p, 1000, 1)}
+    sod["note"] = "latency-bound (800 cells): time per step and per 2000-step solve, not a roofline"
+    out["sod_200x4"] = sod
+    # Couette: each Pr alone and the three as one batch (FP64)
+    cou = {}
+    probs = [wl.couette(Pr, nx=4, ny=200) for Pr in (0.5, 1.0, 2.0)]
+    for Pr, q in zip((0.5, 1.0, 2.0), probs):
+        cou[f"fp64_Pr{Pr:g}"] = config_gpu(lbm, q, lbm.LBM_FP64, 2000, 200, device, hbm)
+    solvers = [lbm.Solver.from_problem(q, device=device) for q in probs]
+    for sv, q in zip(solvers, probs):
+        sv.init(*q.fields())
+    b = lbm.Batch(solvers)
+    b.step(200)
+    stream = torch.cuda.current_stream(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    ev0.record(stream)
+    b.step(2000)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    b.close()
+    for sv in solvers:
+        sv.close()
+    cou["fp64_batch_of_3_us_per_step"] = 1e3 * ev0.elapsed_time(ev1) / 2000
+    cou["oracle"] = {"all_cores": oracle_rate(probs[1], 1000, cores), "one_thread": oracle_rate(probs[1], 1000, 1)}
+    cou["note"] = ("latency-bound (800 cells); a converged solve from rest takes 1e6-1e7 steps "
+                   "(viscous time H^2/nu = 1000 at s5 = 1e3)")
+    out["couette_4x200"] = cou
+    # shock-interface at full size
+    p = wl.shock_interface()
+    si = {"fp64": config_gpu(lbm, p, lbm.LBM_FP64, 20, 3, device, hbm, peak_ops),
+          "fp32": config_gpu(lbm, p, lbm.LBM_FP32_DEV, 200, 5, device, hbm)}
+    si["oracle"] = {"all_cores": oracle_rate(p, 2, cores), "one_thread": oracle_rate(p, 10, 1, crop=(512, 128))}
+    out["shock_interface_4096x1024"] = si
+    # shear layer: the oracle only (the GPU numbers are the headline and fp64 lines)
+    p = wl.shear_layer(N_GRID)
+    out["shear_layer_8192x8192"] = {"oracle": {"all_cores": oracle_rate(p, 2, cores, crop=(2048, 2048)),
+                                               "one_thread": oracle_rate(p, 10, 1, crop=(256, 256))}}
+    orc.set_threads(cores)
+    return out
+
+
+def field_errors(a, b):
+    """FP32 moments a against FP64 moments b: L1 and max relative errors of rho, u (as a vector), T."""
+    import numpy as np
+
+    def rel(x, y):
+        return {"l1": float(np.abs(x - y).sum() / np.abs(y).sum()), "max": float(np.abs(x - y).max() / np.abs(y).max())}
+    du = np.hypot(a[1] - b[1], a[2] - b[2])
+    un = np.hypot(b[1], b[2])
+    return {"rho": rel(a[0], b[0]), "T": rel(a[3], b[3]),
+            "u": {"l1": float(du.sum() / un.sum()), "max": float(du.max() / un.max())}}
+
+
+def precision_study(lbm, p, device, steps, every=None, delta_every=None, periodic=False):
+    """FP32 deviation mode against FP64 on the same fields over `steps` steps: L1 and max relative
+    errors of rho, u, T after the run (and at every `every` steps, the worst), the Delta moments at
+    every `delta_every` steps, the FP32 totals against the FP64 ones, and (doubly periodic grids,
+    where the flux form conserves them) the drift of the totals in each precision."""
+    import numpy as np
+    every = every or steps
+    sol = {prec: lbm.Solver.from_problem(p, precision=prec, device=device)
+           for prec in (lbm.LBM_FP64, lbm.LBM_FP32_DEV)}
+    for sv in sol.values():
+        sv.init(*p.fields())
+    t0 = {prec: sv.totals() for prec, sv in sol.items()}
+    bufs = {prec: _pinned_fields(p.ny, p.nx, 4) for prec in sol}
+    dbufs = {prec: pinned_like(np.zeros((16, p.ny, p.nx))) for prec in sol} if delta_every else None
+    worst = {"rho": {"l1": 0.0, "max": 0.0}, "u": {"l1": 0.0, "max": 0.0}, "T": {"l1": 0.0, "max": 0.0}}
+    dworst = 0.0
+    done = 0
+    tstart = time.perf_counter()
+    while done < steps:
+        n = min(every, steps - done)
+        for sv in sol.values():
+            sv.step(n)
+        done += n
+        want_delta = bool(delta_every) and done % delta_every == 0
+        m = {}
+        for prec, sv in sol.items():
+            f = bufs[prec]
+            d = dbufs[prec][0] if want_delta else None
+            rc = lbm.lbm_moments(sv.h, f[0][0], f[1][0], f[2][0], f[3][0], d)
+            if rc != 0:
+                raise RuntimeError(f"lbm_moments failed ({rc}) at step {done}")
+            m[prec] = [x[0] for x in f]
+        e = field_errors(m[lbm.LBM_FP32_DEV], m[lbm.LBM_FP64])
+        for k in worst:
+            for q in ("l1", "max"):
+                worst[k][q] = max(worst[k][q], e[k][q])
+        if want_delta:
+            d32, d64 = dbufs[lbm.LBM_FP32_DEV][0][4:], dbufs[lbm.LBM_FP64][0][4:]
+            dworst = max(dworst, float(np.abs(d32 - d64).sum() / max(np.abs(d64).sum(), 1e-300)))
+    t1 = {prec: sv.totals() for prec, sv in sol.items()}
+    for sv in sol.values():
+        sv.close()
+    a, b = t1[lbm.LBM_FP32_DEV], t1[lbm.LBM_FP64]
+    out = {"steps": steps, "final": e, "worst_over_checkpoints": worst, "checkpoint_every": every,
+           "totals_fp32_vs_fp64": {"mass": abs(a[0] - b[0]) / abs(b[0]), "momentum_x": abs(a[1] - b[1]) / abs(b[0]),
+                                   "momentum_y": abs(a[2] - b[2]) / abs(b[0]), "energy": abs(a[3] - b[3]) / abs(b[3])},
+           "budget": {"l1": 1e-4, "max": 1e-3, "totals_drift": 1e-6},
+           "seconds": time.perf_counter() - tstart}
+    ok = (max(worst[k]["l1"] for k in worst) <= 1e-4 and max(worst[k]["max"] for k in worst) <= 1e-3
+          and all(np.isfinite([out["final"][k][q] for k in ("rho", "u", "T") for q in ("l1", "max")])))
+    if periodic:   # the flux form conserves the totals exactly on a doubly periodic grid
+        out["totals_drift"] = {"fp32": totals_drift(t0[lbm.LBM_FP32_DEV], a, steps),
+                               "fp64": totals_drift(t0[lbm.LBM_FP64], b, steps)}
+        ok = ok and max(v for k, v in out["totals_drift"]["fp32"].items() if k != "steps") <= 1e-6
+    if delta_every:
+        out["delta_every"] = delta_every
+        out["delta_rows_5_16_l1_worst"] = dworst
+    out["within_budget"] = bool(ok)
+    return out
+
+
 def finish(line, p, args, rank, world):
+    if rank == 0 and args.mode == "both":
+        import torch
+        from paper_1305_4736_gb300 import lbm, workloads as wl
+        dev = torch.cuda.current_device()
+        peaks, _ = measured_peaks()
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        if not args.no_configs:
+            line["configs"] = per_config(lbm, dev, hbm, lbm.lbm_peak_fp64(dev) / 2.0)
+        if not args.no_precision_study:
+            line["precision"] = {
+                f"shear_layer_{p.nx}x{p.ny}": precision_study(lbm, p, dev, 2000, periodic=True),
+                "shock_interface_4096x1024": precision_study(lbm, wl.shock_interface(), dev, 5000, every=100,
+                                                             delta_every=500),
+            }
     if rank == 0 and args.serving_requests > 0:
         import torch
         line["batch"] = batch_measure(torch.cuda.current_device())
-        import torch
-        line["serving"] = serving_measure(args.serving_requests, args.serving_steps, 1024, 256,
-                                          torch.cuda.current_device())
+        line["serving"] = serving_measure(args.serving_requests, args.serving_steps, args.serving_max_grid[0],
+                                          args.serving_max_grid[1], torch.cuda.current_device())
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(p, 1024)
     if world > 1:

@@ -156,11 +156,14 @@ def couette(Pr: float = 1.0, nx: int = 4, ny: int = 200, dx: float | None = None
 
 
 def shock_interface(nx: int = 4096, ny: int = 1024, seed: int = SEED, steps: int = 5000,
-                    p0: float = 1.0) -> Problem:
+                    p0: float = 2.0) -> Problem:
     """Mach-1.5 shock in heavy gas (rho = 4, p = p0) hitting a light gas (rho = 1, p = p0)
     across a sinusoidal interface x_i(y) = 0.6 Lx/4 + 0.02 Ly cos(2 pi y/Ly + phi), phi seeded.
     Lx = 4 Ly, Ly = 1, dx = Ly/ny, dt = 5e-5 (s dt = 0.5 at every size); gamma = 1.4, all s = 1e4;
-    x-lo fixed equilibrium (post-shock), x-hi zero-gradient, periodic y."""
+    x-lo fixed equilibrium (post-shock), x-hi zero-gradient, periodic y.
+    p0 = 2 (T = 0.5 in the heavy gas, 2 in the light gas): at p0 = 1 (T = 0.25) the full-size
+    run (dx = 1/1024, Courant 0.31) goes non-finite about 1300 steps after the shock meets the
+    interface (step ~3600 of 5000; the equilibria are strongly negative at T = 0.25)."""
     gamma = 1.4
     Lx, Ly = 4.0 * (nx / (4 * ny)), 1.0
     dx = Ly / ny
@@ -188,12 +191,15 @@ def shear_layer(n: int = 8192, seed: int = SEED, steps: int = 2000, ny: int | No
     u_x = 0.05 tanh((y - 1/4)/delta) for y < 1/2 and 0.05 tanh((3/4 - y)/delta) above,
     delta = 1/160; v = seeded 8-mode sine perturbation rescaled to max |v| = 1e-3.
     gamma = 1.4, Pr = 0.71: s_5..7 = 5e4, s_8..9 = 3.55e4, others 1e5; dx = 1/n,
-    dt = 1e-5 at every size (s dt <= 1).  `ny` (default n) allows rectangular test grids
-    with the same dx."""
+    dt = min(1e-5, dx/24): 1e-5 up to n = 2400 (s dt <= 1), and a largest Courant number of
+    1/4 above (n = 8192: dt = 5.09e-6, s dt <= 0.51).  At n = 8192 and dt = 1e-5 (Courant
+    0.49, s dt = 1 for the fastest moments) the MC-limited step is unstable: grid-scale noise
+    grows to overflow within a few hundred steps.  `ny` (default n) allows rectangular test
+    grids with the same dx."""
     nx = n
     ny = n if ny is None else ny
     dx = 1.0 / n
-    dt = 1e-5
+    dt = min(1e-5, dx / 24.0)
     rng = np.random.default_rng(seed)
     a = rng.uniform(-1.0, 1.0, 8)
     ph = rng.uniform(0.0, 2.0 * math.pi, 8)
