@@ -107,7 +107,12 @@ typedef struct {
                                       128 columns), 6 = persistent TMA-staged 32 x 16 tiles with
                                       two tile buffers per CTA (LBM_FP32_DEV only), 7 = plain
                                       64-cell tiles (32 x 2; spreads small float64 grids over
-                                      every SM); all agree to round-off (see lbm_autotune) */
+                                      every SM), 8 = LBM_FP64 only: the 32 x 32 TMA-staged tiles
+                                      with the step's arithmetic in double-float form (pairs of
+                                      float32, about 2^-47 rounding per operation) on the float32
+                                      pipe, populations still stored and returned in float64
+                                      (grids of at least 32 x 32); all agree to round-off of
+                                      their arithmetic (see lbm_autotune) */
     double dy;                     /* grid spacing along y; <= 0 means dy = dx.  The y projection
                                       of the convection uses the Courant numbers |v_iy| dt / dy and
                                       the y derivatives of the energy-flux correction divide by
@@ -261,7 +266,7 @@ int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, double dy, vo
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* The lbm_options.step_kernel code (1 .. 7) of the fused-step kernel this context runs
+/* The lbm_options.step_kernel code (1 .. 8) of the fused-step kernel this context runs
    (after automatic selection or lbm_autotune); -1 for a NULL context. */
 int lbm_step_kernel(const lbm_ctx *ctx);
 

@@ -15,9 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_step_tma.cu", "lbm_step_stream.cu", "lbm_peak.cu",
-           "lbm_noalloc.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_internal.h", "lbm_tma_util.cuh"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_step_tma.cu", "lbm_step_stream.cu", "lbm_step_dd.cu",
+           "lbm_peak.cu", "lbm_noalloc.cu"]
+HEADERS = ["lbm_dd.cuh", "lbm_device.cuh", "lbm_internal.h", "lbm_tma_util.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          f"-I{os.path.join(ROOT, 'include')}"]

@@ -46,6 +46,8 @@ struct lbm_ctx {
     bool use_tma = false;
     bool use_stream = false;
     bool use_pipe = false;
+    bool use_dd = false;          // float64 mode in double-float arithmetic (step_kernel 8)
+    lbm::Coef<lbm::dd> cdd{};     // its coefficients
     int plain_ty = lbm::kTY;      // tile height of the plain step kernel
     CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
     CUtensorMap smap[2];          // row-copy descriptors (streaming kernel)
@@ -292,11 +294,20 @@ bool tma_ready(lbm_ctx *c)
 
 // The TMA-staged tile kernel takes the x halo of tiles at a periodic x edge from the wrapped
 // interior itself: on a grid periodic in x it needs only the ghost rows.
-bool ghost_rows_only(const lbm_ctx *c) { return c->use_tma && (c->P.wrap & 1); }
+bool ghost_rows_only(const lbm_ctx *c) { return (c->use_tma || c->use_dd) && (c->P.wrap & 1); }
+
+// The double-float float64 kernel: the float64 tile maps and the Coef<dd> of the context.
+bool dd_ready(lbm_ctx *c)
+{
+    if (c->prec != LBM_FP64 || !lbm::tma_supported(c->P, LBM_FP64) || lbm::dd_prepare() != cudaSuccess) return false;
+    lbm::coef_dd(c->P, &c->cdd);
+    return make_tile_maps(c);
+}
 
 // One fused step of context c from buffer `in` into buffer in ^ 1, on stream st.
 cudaError_t launch_fused_step(lbm_ctx *c, int in, cudaStream_t st)
 {
+    if (c->use_dd) return lbm::launch_step_dd(c->P, &c->cdd, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_pipe) return lbm::launch_step_tma_pipe(c->P, &c->pmap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_stream) return lbm::launch_step_stream(c->P, c->prec, &c->smap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
@@ -476,7 +487,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->tma_err = c->flag + 1;
     c->init_err = c->flag + 2;
     int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 7) {
+    if (want < 0 || want > 8) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
@@ -508,14 +519,16 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     // grids of at least 32 waves of its tiles (2048 cells per SM a wave): there the kernel's
     // extra loads in edge tiles cost less than the ghost columns' copy; on smaller grids a
     // kernel lasts as long as its slowest tiles, which the extra loads lengthen
-    if (c->use_tma && bc->xlo.kind == LBM_BC_PERIODIC) {
+    if (want == 8 && dd_ready(c)) c->use_dd = true;
+    if ((c->use_tma || c->use_dd) && bc->xlo.kind == LBM_BC_PERIODIC) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         if (sms < 1) sms = 152;
         if ((long long)nx * ny >= 32LL * 2048 * sms) c->P.wrap = 1;
     }
     if (want == 6 && pipe_ready(c)) c->use_pipe = true;
-    if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream) || (want == 6 && !c->use_pipe)) {
+    if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream) || (want == 6 && !c->use_pipe) ||
+        (want == 8 && !c->use_dd)) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "requested step kernel unavailable for this grid or driver");
     }
@@ -907,8 +920,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 7 = plain 64-cell tiles,
-    // 2 = TMA-staged, 5 = streaming, 6 = double-buffered TMA-staged 32x16 (float32)
-    int cands[7] = {1, 3, 4, 7, 0, 0, 0};
+    // 2 = TMA-staged, 5 = streaming, 6 = double-buffered TMA-staged 32x16 (float32),
+    // 8 = double-float TMA-staged (float64)
+    int cands[8] = {1, 3, 4, 7, 0, 0, 0, 0};
     int ncand = 4;
     const bool tma_ok = c->use_tma || tma_ready(c);
     cudaGetLastError();
@@ -919,6 +933,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     const bool pipe_ok = c->use_pipe || pipe_ready(c);
     cudaGetLastError();
     if (pipe_ok) cands[ncand++] = 6;
+    const bool dd_ok = c->use_dd || dd_ready(c);
+    cudaGetLastError();
+    if (dd_ok) cands[ncand++] = 8;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
@@ -929,6 +946,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     for (int k = 0; k < ncand && ce == cudaSuccess; k++) {
         auto run = [&]() {
             const int cd = cands[k];
+            if (cd == 8)
+                return lbm::launch_step_dd(c->P, &c->cdd, &c->tmap[c->cur], c->f[c->cur], c->f[c->cur ^ 1],
+                                           c->tma_err, c->stream);
             if (cd == 6)
                 return lbm::launch_step_tma_pipe(c->P, &c->pmap[c->cur], c->f[c->cur ^ 1], c->tma_err, c->stream);
             if (cd == 5)
@@ -956,6 +976,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     c->use_tma = best_c == 2;
     c->use_stream = best_c == 5;
     c->use_pipe = best_c == 6;
+    c->use_dd = best_c == 8;
     c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : (best_c == 7 ? 2 : 8));
     if (choice) *choice = best_c;
     return LBM_OK;
@@ -966,6 +987,7 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 int lbm_step_kernel(const lbm_ctx *c)
 {
     if (!c) return -1;
+    if (c->use_dd) return 8;
     if (c->use_pipe) return 6;
     if (c->use_stream) return 5;
     if (c->use_tma) return 2;
@@ -1053,7 +1075,7 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
 // launch serves them all.
 bool batch_solo(const lbm_ctx *c, int sms)
 {
-    return (c->use_tma || c->use_stream || c->use_pipe) && (long long)c->P.nx * c->P.ny >= 512LL * sms;
+    return (c->use_tma || c->use_stream || c->use_pipe || c->use_dd) && (long long)c->P.nx * c->P.ny >= 512LL * sms;
 }
 
 }  // namespace

@@ -1,0 +1,205 @@
+// lbm_dd.cuh -- double-float arithmetic for the float64 mode on the float32 pipe.
+//
+// GB300 issues float32 FMAs at 128 lanes per SM cycle and float64 ones at about 1.7, so the
+// float64 mode's step can run faster in double-float arithmetic: a value is an unevaluated sum
+// hi + lo of two float32 numbers with |lo| <= ulp(hi) / 2 (48 significand bits), and each
+// operation is built from error-free transformations on the float32 pipe (Dekker, "A
+// floating-point technique for extending the available precision", Numer. Math. 18, 1971;
+// Knuth, TAOCP vol. 2, 4.2.2: TwoSum; Fast2Sum; the product error from an FMA).  Relative
+// rounding of an operation is about 2^-47, against 2^-53 in float64.  The populations stay
+// float64 in HBM: a staged value is split into hi + lo (rounded to nearest, with integer
+// operations) and an updated value is rounded back to float64 (integer operations as well;
+// float32 <-> float64 conversions run at the float64 rate on this part).
+//
+// Every float32 operation here uses the _rn intrinsics, which the compiler neither contracts
+// into FMAs nor reorders, so the transformations stay error-free.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct dd {
+    float hi, lo;
+};
+
+// Host: the double-float value nearest to x (hi = x rounded to float, lo = the rest rounded).
+inline dd dd_host(double x)
+{
+    const float h = (float)x;
+    return dd{h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ dd ddf(float h) { return dd{h, 0.0f}; }
+
+// Fast2Sum (|a| >= |b| or a == 0): s + e = a + b exactly.
+__device__ __forceinline__ dd fast2sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return dd{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a + b: TwoSum of the high parts, the low parts added to its error, renormalised (11 operations).
+__device__ __forceinline__ dd operator+(dd a, dd b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    return fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dd operator-(dd a, dd b)
+{
+    const float s = __fsub_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fadd_rn(b.hi, v));
+    return fast2sum(s, __fadd_rn(e, __fsub_rn(a.lo, b.lo)));
+}
+
+// a * b: the exact product of the high parts (its error from an FMA) plus the cross terms (7).
+__device__ __forceinline__ dd operator*(dd a, dd b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast2sum(p, e);
+}
+
+// a * c for a float32 constant c (6).
+__device__ __forceinline__ dd operator*(dd a, float c)
+{
+    const float p = __fmul_rn(a.hi, c);
+    float e = __fmaf_rn(a.hi, c, -p);
+    e = __fmaf_rn(a.lo, c, e);
+    return fast2sum(p, e);
+}
+__device__ __forceinline__ dd operator*(float c, dd a) { return a * c; }
+
+// a * 2^k (exact).
+__device__ __forceinline__ dd scale2(dd a, float p2) { return dd{__fmul_rn(a.hi, p2), __fmul_rn(a.lo, p2)}; }
+
+__device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
+__device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
+
+// a * b + c (15).
+__device__ __forceinline__ dd fma_dd(dd a, dd b, dd c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(p, c.hi);
+    const float v = __fsub_rn(s, p);
+    const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
+    return fast2sum(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
+}
+
+// 1/x: the float32 approximate reciprocal y (relative error below 2^-22), then one Newton step
+// y + y (1 - x y) with 1 - x y formed in double-float; relative error about 2^-44.
+__device__ __forceinline__ dd recip(dd x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.hi));
+    const dd r = ddf(1.0f) - x * y;
+    return fast2sum(y, __fmul_rn(y, r.hi));
+}
+
+// Lexicographic order of normalised values (hi decides, lo breaks ties).
+__device__ __forceinline__ bool dd_lt(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// Twice the MC slope, 2 minmod(2a, (a + b)/2, 2b) = sign(a) min(4|a|, 4|b|, |a + b|) when a and
+// b agree in sign and 0 otherwise (Sec. III, reading A6); as mc2 of lbm_device.cuh.
+__device__ __forceinline__ dd mc2(dd a, dd b)
+{
+    const dd s = a + b;
+    const unsigned sa = __float_as_uint(a.hi), sb = __float_as_uint(b.hi);
+    const bool agree = ((sa ^ sb) >> 31) == 0u && a.hi != 0.0f && b.hi != 0.0f;
+    // work on magnitudes: flip all three when a < 0 (then b, s < 0 as well)
+    const float sg = (sa >> 31) ? -1.0f : 1.0f;
+    const dd A = dd{a.hi * sg, a.lo * sg}, B = dd{b.hi * sg, b.lo * sg}, S = dd{s.hi * sg, s.lo * sg};
+    const dd m = dd_lt(A, B) ? A : B;
+    const dd m4 = scale2(m, 4.0f);
+    const dd r = dd_lt(m4, S) ? m4 : S;
+    return agree ? dd{r.hi * sg, r.lo * sg} : dd{0.0f, 0.0f};
+}
+
+// ---------------------------------------------------------------------------
+// float64 <-> double-float with integer operations.
+// ---------------------------------------------------------------------------
+// x = hi + lo with hi = x rounded to 24 significand bits (half away from zero) and lo the rest
+// rounded to float32 (|lo| <= 2^-25 |x|; the pair carries 48 of x's 53 bits, rounded to
+// nearest).  |x| below 2^-74 (5.3e-23) is flushed to zero: populations here are O(1), so the
+// absolute error stays below that.  Non-finite x and |x| >= 2^127 give +-inf or NaN in hi.
+__device__ __forceinline__ dd dd_split(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned ex = (hw >> 20) & 0x7FFu;
+    const unsigned sign = hw & 0x80000000u;
+    if (ex < 949u) return dd{0.0f, 0.0f};
+    if (ex >= 1150u) {
+        const bool nan = ex == 2047u && ((hw & 0xFFFFFu) | lw) != 0u;
+        return dd{__uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.0f};
+    }
+    // top 24 significand bits with the exponent rebiased (1023 -> 127); a carry from the
+    // rounding increment moves into the exponent field, as it should
+    unsigned fb = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
+    const unsigned up = (lw >> 28) & 1u;
+    fb += up;
+    // remainder in units of 2^(ex - 1075): the low 29 bits, less 2^29 when hi was rounded up
+    const int r = (int)(lw & 0x1FFFFFFFu) - (int)(up << 29);
+    const float scale = __uint_as_float((ex - 948u) << 23);   // 2^(ex - 1075), a normal float
+    const float lo = __fmul_rn(__int2float_rn(r), scale);
+    return dd{__uint_as_float(fb | sign), __uint_as_float(__float_as_uint(lo) ^ sign)};
+}
+
+// hi + lo rounded to float64.  The sum is exact in float64 whenever lo's exponent is within
+// 29 of hi's (the usual case after fast2sum); below that the part of lo beneath hi's float64
+// ulp is rounded half up.  hi == 0 returns lo; zero and subnormal float32 parts count as 0.
+__device__ __forceinline__ double dd_to_double(dd v)
+{
+    unsigned hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
+    unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
+    if (eh == 0u) {   // hi is zero (or subnormal): the value is lo
+        hb = lb;
+        eh = el;
+        el = 0u;
+        if (eh == 0u) return __longlong_as_double((long long)((unsigned long long)(hb & 0x80000000u) << 32));
+    }
+    if (eh == 0xFFu) {   // inf / NaN: keep it non-finite
+        return __longlong_as_double((long long)(((unsigned long long)(hb & 0x80000000u) << 32) |
+                                                0x7FF8000000000000ull));
+    }
+    // significands with the implicit bit, in units of hi's float64 ulp: hi -> 24 bits << 29
+    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    int e = (int)eh;
+    if (el != 0u) {
+        const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+        const int k = (int)eh - (int)el;                      // >= 24 for a normalised pair
+        unsigned long long c;
+        if (k <= 29) c = ml << (29 - k);
+        else if (k - 29 < 40) c = (ml + (1ull << (k - 30))) >> (k - 29);
+        else c = 0ull;
+        if ((hb ^ lb) & 0x80000000u) {
+            M -= c;
+            if (M < (1ull << 52)) {   // hi was a power of two: one bit of normalisation
+                M <<= 1;
+                e -= 1;
+            }
+        } else {
+            M += c;
+            if (M >= (1ull << 53)) {  // not reached by a normalised pair; kept for safety
+                M = (M + 1ull) >> 1;
+                e += 1;
+            }
+        }
+    }
+    const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                                    ((unsigned long long)(e + 896) << 52) | (M & ((1ull << 52) - 1ull));
+    return __longlong_as_double((long long)bits);
+}
+
+}  // namespace lbm

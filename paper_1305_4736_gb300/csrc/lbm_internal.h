@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_dd.cuh"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -124,6 +125,14 @@ bool stream_supported(const Params &P);
 cudaError_t stream_prepare();
 // `tmap` points to the CUtensorMap of the input buffer with box BW x 1 x 16.
 cudaError_t launch_step_stream(const Params &P, int prec, const void *tmap, void *fout, int *err, cudaStream_t st);
+
+// Float64-mode step in double-float arithmetic on the float32 pipe (step_kernel 8): the tiles
+// and tensor maps of the float64 TMA-staged kernel; `coef` is the Coef<dd> of the context
+// (coef_dd).
+void coef_dd(const Params &P, Coef<dd> *out);
+cudaError_t dd_prepare();
+cudaError_t launch_step_dd(const Params &P, const void *coef, const void *tmap, const void *fin, void *fout,
+                           int *err, cudaStream_t st);
 
 // Sustained float64 FMA rate of the current device in FLOP/s (FMA = 2).
 cudaError_t measure_fp64_fma(double *flops);

@@ -68,6 +68,34 @@ __device__ __forceinline__ R slope2(R a, R b)
     return Lim == 0 ? mc2(a, b) : (Lim == 1 ? R(2.0) * b : R(0.0));
 }
 
+// x halo of a tile at a periodic x edge: the staged cells left of column 0 or right of column
+// nx-1 (the ghost columns, and columns beyond them in a ragged last tile) take the values of
+// the wrapped interior cells of fin, as the periodic ghost fill would have written them.  The
+// ghost rows come from the ghost fill (contiguous rows, cheap to copy); cells outside along
+// both axes are corners of the ring, which the cross stencil of stored cells never reads.
+template <typename R>
+__device__ __noinline__ void wrap_halo(const Params &P, const R *__restrict__ fin, R *tile, int x0, int y0, int tid,
+                                       int nthreads)
+{
+    using S = TmaShape<R>;
+    for (int k = tid; k < S::SW * S::SH; k += nthreads) {
+        const int c = k % S::SW, r = k / S::SW;
+        const int x = x0 + c - S::HX, y = y0 + r - 2;
+        if (!(x < 0 || x >= P.nx) || y < 0 || y >= P.ny) continue;
+        const int xs = ((x % P.nx) + P.nx) % P.nx;
+        const long long src = (long long)(y + OY) * P.pitch + (xs + OX);
+        if constexpr (sizeof(R) == sizeof(float)) {
+            const float2 *f2 = reinterpret_cast<const float2 *>(fin);
+            float2 *t2 = reinterpret_cast<float2 *>(tile);
+#pragma unroll
+            for (int pr = 0; pr < 8; pr++) t2[pr * S::PL + k] = f2[pr * P.plane + src];
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; q++) tile[q * S::PL + k] = fin[q * P.plane + src];
+        }
+    }
+}
+
 // ---- packed float32 pairs (Blackwell f32x2 arithmetic) -------------------
 // Populations q and q + 4 (q = 0..3 axis shells 1 and 2, q = 8..11 diagonal shells 3 and 4)
 // move in the same direction: their stencils have the same offsets and only the per-shell

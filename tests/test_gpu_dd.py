@@ -1,0 +1,149 @@
+"""GPU parity of the double-float float64 kernel (lbm_options.step_kernel = 8).
+
+The populations stay float64; the step's arithmetic runs in double-float form on the float32
+pipe (about 2^-47 rounding per operation instead of 2^-53).  The bar is the float64 mode's:
+max relative error <= 1e-10 on rho, u, T against the oracle (u as a vector), here also on the
+populations themselves, for every limiter, with walls and the energy-flux correction active
+(Pr != 1), with dy != dx, on ragged tiles, after 1000 steps of the reduced shock-interface
+and shear-layer configurations, and at full size (8192^2, sampled cells recomputed by the
+oracle from the GPU's previous step).  Against the float64 tile kernel it agrees to a few
+parts in 1e13 after 60 steps.
+"""
+import numpy as np
+import pytest
+
+from _gpu_helpers import fp64_errors
+from paper_1305_4736_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1305_4736_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def _run(lbm, p, steps, kernel=8, limiter=None):
+    s = lbm.Solver(p.nx, p.ny, p.dx, p.dt, p.gamma, p.Pr, p.s, p.limiter if limiter is None else limiter, p.bc,
+                   step_kernel=kernel, dy=p.dy)
+    assert s.step_kernel == kernel
+    s.init(*p.fields())
+    s.step(steps)
+    return s
+
+
+def _oracle(orc, p, steps, limiter=None):
+    O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, p.limiter if limiter is None else limiter, p.bc, dy=p.dy)
+    O.init(*p.fields())
+    O.step(steps)
+    return O
+
+
+def _check(s, O):
+    errs = fp64_errors(s, O)
+    for k, v in errs.items():
+        assert v <= TOL, f"{k}: {v:.3e} ({errs})"
+    fo = O.get_state()
+    assert np.abs(s.get_state() - fo).max() <= TOL * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_dd_kernel_each_limiter_against_oracle(orc, lbm, limiter):
+    p = wl.shock_interface(nx=150, ny=70, steps=120)          # ragged against 32 x 32 tiles
+    _check(_run(lbm, p, 120, limiter=limiter), _oracle(orc, p, 120, limiter))
+
+
+def test_dd_kernel_walls_and_energy_flux_correction(orc, lbm):
+    """NEQ walls on x (moving, heated), equilibrium and zero-gradient y edges, Pr = 0.71."""
+    p = wl.shear_layer(96, ny=66)
+    p.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
+    _check(_run(lbm, p, 300), _oracle(orc, p, 300))
+
+
+@pytest.mark.parametrize("Pr", [0.5, 2.0])
+def test_dd_kernel_couette_1000_steps(orc, lbm, Pr):
+    p = wl.couette(Pr, nx=32, ny=200)
+    _check(_run(lbm, p, 1000), _oracle(orc, p, 1000))
+
+
+@pytest.mark.parametrize("ratio", [0.7, 1.6])
+def test_dd_kernel_dy_not_dx(orc, lbm, ratio):
+    p = wl.shear_layer(100, ny=70)
+    p.dy = ratio * p.dx
+    _check(_run(lbm, p, 200), _oracle(orc, p, 200))
+
+
+def test_dd_kernel_periodic_x_wrap(lbm):
+    """A grid large enough for the in-kernel x wrap of periodic edge tiles (ghost launch copies
+    only the ghost rows), against the float64 tile kernel after 20 steps."""
+    p = wl.shear_layer(3000, ny=3500)
+    s = _run(lbm, p, 20)
+    t = _run(lbm, p, 20, kernel=2)
+    a, b = s.get_state_rows(0, p.ny), t.get_state_rows(0, p.ny)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_dd_kernel_matches_float64_tile_kernel(lbm, limiter):
+    p = wl.shock_interface(nx=150, ny=70, steps=60)
+    a = _run(lbm, p, 60, kernel=8, limiter=limiter).get_state()
+    b = _run(lbm, p, 60, kernel=2, limiter=limiter).get_state()
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("name", ["shock_interface_512x128", "shear_layer_1024x1024"])
+def test_dd_kernel_reduced_configs_1000_steps(orc, lbm, name):
+    p = (wl.shock_interface(nx=512, ny=128, steps=1000) if name.startswith("shock")
+         else wl.shear_layer(1024, steps=1000))
+    s = _run(lbm, p, 1000)
+    O = _oracle(orc, p, 1000)
+    errs = fp64_errors(s, O)
+    for k, v in errs.items():
+        assert v <= TOL, f"{k}: {v:.3e} ({errs})"
+
+
+def test_dd_kernel_rejected_in_fp32_mode(lbm):
+    p = wl.shear_layer(64, ny=32)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver.from_problem(p, precision=1, step_kernel=8)
+
+
+def test_dd_kernel_autotune_candidate(lbm):
+    p = wl.shear_layer(512, ny=256)
+    s = lbm.Solver.from_problem(p)
+    s.init(*p.fields())
+    choice = s.autotune(reps=3)
+    assert choice in (1, 2, 3, 4, 5, 7, 8) and s.step_kernel == choice
+    s.close()
+
+
+def test_dd_kernel_full_size_sampled(orc, lbm):
+    """8192 x 8192 shear layer on the double-float kernel: after 3 steps, 64 seeded cells of
+    step 4 are recomputed by the oracle from the GPU's step-3 rows; 1e-13 of f."""
+    from test_gpu_parity import _patch
+    p = wl.shear_layer(8192)
+    s = lbm.Solver.from_problem(p, step_kernel=8)
+    assert s.step_kernel == 8
+    s.init(*p.fields())
+    s.step(3)
+    rng = np.random.default_rng(7)
+    ys = rng.integers(2, p.ny - 2, 64)
+    xs = rng.integers(0, p.nx, 64)
+    before = {int(y): s.get_state_rows(int(y) - 2, 5) for y in set(ys.tolist())}
+    s.step(1)
+    worst = 0.0
+    for y, x in zip(ys.tolist(), xs.tolist()):
+        want = orc.update_patch(_patch(before[y], 2, x, p.nx), p.dx, p.dt, p.gamma, p.s, p.limiter)
+        got = s.get_state_rows(y, 1)[:, 0, x]
+        worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
+    s.close()
+    assert worst <= 1e-13, worst
