@@ -214,7 +214,7 @@ def pinned_like(a):
 # ------------------------------------------------------------------------- GPU arm
 KERNEL_NAMES = {1: "k_step<{r},{d},MC,256>", 2: "k_step_tma<{r},{d},MC>", 3: "k_step<{r},{d},MC,128>",
                 4: "k_step<{r},{d},MC,512>", 5: "k_step_stream<{r},{d},MC>", 6: "k_step_tma_pipe<{r},{d},MC>",
-                7: "k_step<{r},{d},MC,64>"}
+                7: "k_step<{r},{d},MC,64>", 8: "k_step_dd<MC>"}
 
 
 def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):
@@ -697,6 +697,14 @@ def precision_study(lbm, p, device, steps, every=None, delta_every=None, periodi
     return out
 
 
+def guarded(fn, *a, **kw):
+    """Run one measurement section; a failure is reported in the line instead of ending the run."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:   # noqa: BLE001 -- reported, not swallowed
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def finish(line, p, args, rank, world):
     if rank == 0 and args.mode == "both":
         import torch
@@ -705,18 +713,18 @@ def finish(line, p, args, rank, world):
         peaks, _ = measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         if not args.no_configs:
-            line["configs"] = per_config(lbm, dev, hbm, lbm.lbm_peak_fp64(dev) / 2.0)
+            line["configs"] = guarded(per_config, lbm, dev, hbm, lbm.lbm_peak_fp64(dev) / 2.0)
         if not args.no_precision_study:
             line["precision"] = {
-                f"shear_layer_{p.nx}x{p.ny}": precision_study(lbm, p, dev, 2000, periodic=True),
-                "shock_interface_4096x1024": precision_study(lbm, wl.shock_interface(), dev, 5000, every=100,
-                                                             delta_every=500),
+                f"shear_layer_{p.nx}x{p.ny}": guarded(precision_study, lbm, p, dev, 2000, periodic=True),
+                "shock_interface_4096x1024": guarded(precision_study, lbm, wl.shock_interface(), dev, 5000,
+                                                     every=100, delta_every=500),
             }
     if rank == 0 and args.serving_requests > 0:
         import torch
-        line["batch"] = batch_measure(torch.cuda.current_device())
-        line["serving"] = serving_measure(args.serving_requests, args.serving_steps, args.serving_max_grid[0],
-                                          args.serving_max_grid[1], torch.cuda.current_device())
+        line["batch"] = guarded(batch_measure, torch.cuda.current_device())
+        line["serving"] = guarded(serving_measure, args.serving_requests, args.serving_steps,
+                                  args.serving_max_grid[0], args.serving_max_grid[1], torch.cuda.current_device())
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_run(p, 1024)
     if world > 1:
