@@ -2,11 +2,18 @@
 //
 // GB300 issues float32 FMAs at 128 lanes per SM cycle and float64 ones at about 1.7, so the
 // float64 mode's step can run faster in double-float arithmetic: a value is an unevaluated sum
-// hi + lo of two float32 numbers with |lo| <= ulp(hi) / 2 (48 significand bits), and each
-// operation is built from error-free transformations on the float32 pipe (Dekker, "A
-// floating-point technique for extending the available precision", Numer. Math. 18, 1971;
-// Knuth, TAOCP vol. 2, 4.2.2: TwoSum; Fast2Sum; the product error from an FMA).  Relative
-// rounding of an operation is about 2^-47, against 2^-53 in float64.  The populations stay
+// hi + lo of two float32 numbers (48 significand bits), and each operation is built from
+// error-free transformations on the float32 pipe (Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18, 1971; Knuth, TAOCP vol. 2, 4.2.2:
+// TwoSum; Fast2Sum; the product error from an FMA).  Relative rounding of an operation is
+// about 2^-47, against 2^-53 in float64.
+//
+// Values are kept unnormalised between operations: a sum or product returns the high part and
+// its exact error plus the low parts, without the final Fast2Sum that would make
+// |lo| <= ulp(hi) / 2.  The pair still holds the value to the same accuracy (lo stays within a
+// few units of 2^-24 of the operands' magnitudes), and every operation here reads both parts,
+// so only the places that look at hi alone renormalise first: the MC slope's comparisons and
+// sign test, the reciprocal's Newton step, and the rounding to float64.  The populations stay
 // float64 in HBM: a staged value is split into hi + lo (rounded to nearest, with integer
 // operations) and an updated value is rounded back to float64 (integer operations as well;
 // float32 <-> float64 conversions run at the float64 rate on this part).
@@ -39,13 +46,13 @@ __device__ __forceinline__ dd fast2sum(float a, float b)
     return dd{s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
-// a + b: TwoSum of the high parts, the low parts added to its error, renormalised (11 operations).
+// a + b: TwoSum of the high parts, the low parts added to its error (8 operations).
 __device__ __forceinline__ dd operator+(dd a, dd b)
 {
     const float s = __fadd_rn(a.hi, b.hi);
     const float v = __fsub_rn(s, a.hi);
     const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-    return fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+    return dd{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 
 __device__ __forceinline__ dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
@@ -55,26 +62,27 @@ __device__ __forceinline__ dd operator-(dd a, dd b)
     const float s = __fsub_rn(a.hi, b.hi);
     const float v = __fsub_rn(s, a.hi);
     const float e = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fadd_rn(b.hi, v));
-    return fast2sum(s, __fadd_rn(e, __fsub_rn(a.lo, b.lo)));
+    return dd{s, __fadd_rn(e, __fsub_rn(a.lo, b.lo))};
 }
 
-// a * b: the exact product of the high parts (its error from an FMA) plus the cross terms (7).
+// a * b: the product of the high parts and its exact error (from an FMA) plus the cross
+// terms (4 operations).
 __device__ __forceinline__ dd operator*(dd a, dd b)
 {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return fast2sum(p, e);
+    return dd{p, e};
 }
 
-// a * c for a float32 constant c (6).
+// a * c for a float32 constant c (3).
 __device__ __forceinline__ dd operator*(dd a, float c)
 {
     const float p = __fmul_rn(a.hi, c);
     float e = __fmaf_rn(a.hi, c, -p);
     e = __fmaf_rn(a.lo, c, e);
-    return fast2sum(p, e);
+    return dd{p, e};
 }
 __device__ __forceinline__ dd operator*(float c, dd a) { return a * c; }
 
@@ -84,7 +92,7 @@ __device__ __forceinline__ dd scale2(dd a, float p2) { return dd{__fmul_rn(a.hi,
 __device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
 __device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
 
-// a * b + c (15).
+// a * b + c (12).
 __device__ __forceinline__ dd fma_dd(dd a, dd b, dd c)
 {
     const float p = __fmul_rn(a.hi, b.hi);
@@ -94,27 +102,35 @@ __device__ __forceinline__ dd fma_dd(dd a, dd b, dd c)
     const float s = __fadd_rn(p, c.hi);
     const float v = __fsub_rn(s, p);
     const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
-    return fast2sum(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
+    return dd{s, __fadd_rn(t, __fadd_rn(e, c.lo))};
 }
 
-// 1/x: the float32 approximate reciprocal y (relative error below 2^-22), then one Newton step
-// y + y (1 - x y) with 1 - x y formed in double-float; relative error about 2^-44.
+// 1/x: the float32 approximate reciprocal y of x rounded to float (relative error below
+// 2^-22), then one Newton step y + y (1 - x y) with 1 - x y formed in double-float and its two
+// parts summed (the residual's high part alone can be of the size of its low part); relative
+// error about 2^-44.
 __device__ __forceinline__ dd recip(dd x)
 {
     float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.hi));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fadd_rn(x.hi, x.lo)));
     const dd r = ddf(1.0f) - x * y;
-    return fast2sum(y, __fmul_rn(y, r.hi));
+    return fast2sum(y, __fmul_rn(y, __fadd_rn(r.hi, r.lo)));
 }
 
 // Lexicographic order of normalised values (hi decides, lo breaks ties).
 __device__ __forceinline__ bool dd_lt(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
 // Twice the MC slope, 2 minmod(2a, (a + b)/2, 2b) = sign(a) min(4|a|, 4|b|, |a + b|) when a and
-// b agree in sign and 0 otherwise (Sec. III, reading A6); as mc2 of lbm_device.cuh.
+// b agree in sign and 0 otherwise (Sec. III, reading A6); as mc2 of lbm_device.cuh.  The
+// inputs and their sum are renormalised first (Fast2Sum with a low part larger than the high
+// part, after a cancellation, still returns the pair's value to within 2^-24 of that low part,
+// far below the pair's own accuracy).
 __device__ __forceinline__ dd mc2(dd a, dd b)
 {
-    const dd s = a + b;
+    a = fast2sum(a.hi, a.lo);
+    b = fast2sum(b.hi, b.lo);
+    dd s = a + b;
+    s = fast2sum(s.hi, s.lo);
     const unsigned sa = __float_as_uint(a.hi), sb = __float_as_uint(b.hi);
     const bool agree = ((sa ^ sb) >> 31) == 0u && a.hi != 0.0f && b.hi != 0.0f;
     // work on magnitudes: flip all three when a < 0 (then b, s < 0 as well)
@@ -156,11 +172,13 @@ __device__ __forceinline__ dd dd_split(double x)
     return dd{__uint_as_float(fb | sign), __uint_as_float(__float_as_uint(lo) ^ sign)};
 }
 
-// hi + lo rounded to float64.  The sum is exact in float64 whenever lo's exponent is within
-// 29 of hi's (the usual case after fast2sum); below that the part of lo beneath hi's float64
-// ulp is rounded half up.  hi == 0 returns lo; zero and subnormal float32 parts count as 0.
+// hi + lo rounded to float64, after renormalising the pair.  The sum is exact in float64
+// whenever lo's exponent is within 29 of hi's (the usual case); below that the part of lo
+// beneath hi's float64 ulp is rounded half up.  hi == 0 returns lo; zero and subnormal float32
+// parts count as 0.
 __device__ __forceinline__ double dd_to_double(dd v)
 {
+    v = fast2sum(v.hi, v.lo);
     unsigned hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
     unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
     if (eh == 0u) {   // hi is zero (or subnormal): the value is lo
