@@ -93,9 +93,11 @@ typedef struct {
     void *stream;                  /* cudaStream_t; NULL = the legacy default stream */
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
-    int step_kernel;               /* fused-step kernel: 0 = automatic (float64: streaming on grids
-                                      that give every SM at least 32 rows of a 256-column strip
-                                      and have at least 4M cells, else plain 64-cell tiles;
+    int step_kernel;               /* fused-step kernel: 0 = automatic (float64: the double-float
+                                      kernel 8 on grids of at least 32 x 32; narrower grids:
+                                      streaming on grids that give every SM at least 32 rows of a
+                                      256-column strip and have at least 4M cells, else plain
+                                      64-cell tiles;
                                       float32: TMA-staged where the grid allows, else plain
                                       32 x 8), 1 = plain 32 x 8 tiles (grids narrower than 32
                                       columns: TX x NT/TX tiles of the same NT threads, TX the

@@ -494,11 +494,15 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     if (want == 3) c->plain_ty = 4;
     if (want == 4) c->plain_ty = 16;
     if (want == 7) c->plain_ty = 2;
-    // automatic, float64 (bound by the float64 pipe, about 1.6 lane operations per cycle per
-    // SM on GB300): the streaming kernel when the grid gives every SM at least 32 rows of a
+    // automatic, float64: the double-float kernel wherever its 32 x 32 tiles fit (on GB300 the
+    // float32 pipe runs its arithmetic 2-2.5x faster than the float64 kernels run theirs, from
+    // 256 x 256 cells up); on narrower grids the float64 pipe (about 1.6 lane operations per
+    // cycle per SM): the streaming kernel when the grid gives every SM at least 32 rows of a
     // 256-column strip; else the plain kernel, on 256-cell tiles when they still give every SM
     // four tiles (their flow-velocity ring costs less), on 64-cell tiles below that, which
     // spread a small grid's float64 work over more SMs
+    if (want == 0 && prec == LBM_FP64 && dd_ready(c)) want = 8;
+    cudaGetLastError();
     if (want == 0 && prec == LBM_FP64) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);

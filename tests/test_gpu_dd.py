@@ -111,6 +111,18 @@ def test_dd_kernel_reduced_configs_1000_steps(orc, lbm, name):
         assert v <= TOL, f"{k}: {v:.3e} ({errs})"
 
 
+@pytest.mark.parametrize("nx,ny,want", [(256, 256, 8), (33, 32, 8), (31, 64, 7), (200, 4, 7), (4, 200, 7)])
+def test_automatic_float64_choice(lbm, nx, ny, want):
+    """The double-float kernel is the automatic float64 choice wherever its 32 x 32 tiles fit;
+    narrower grids keep the float64-pipe kernels."""
+    p = wl.shear_layer(max(nx, ny), ny=ny)
+    p.nx = nx
+    p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:, :nx]) for a in (p.rho, p.ux, p.uy, p.T))
+    s = lbm.Solver.from_problem(p)
+    assert s.step_kernel == want
+    s.close()
+
+
 def test_dd_kernel_rejected_in_fp32_mode(lbm):
     p = wl.shear_layer(64, ny=32)
     with pytest.raises(lbm.LbmError):
@@ -127,11 +139,12 @@ def test_dd_kernel_autotune_candidate(lbm):
 
 
 def test_dd_kernel_full_size_sampled(orc, lbm):
-    """8192 x 8192 shear layer on the double-float kernel: after 3 steps, 64 seeded cells of
-    step 4 are recomputed by the oracle from the GPU's step-3 rows; 1e-13 of f."""
+    """8192 x 8192 shear layer in the benchmark's float64 launch configuration (the automatic
+    choice is the double-float kernel): after 3 steps, 64 seeded cells of step 4 are
+    recomputed by the oracle from the GPU's step-3 rows; 1e-13 of f."""
     from test_gpu_parity import _patch
     p = wl.shear_layer(8192)
-    s = lbm.Solver.from_problem(p, step_kernel=8)
+    s = lbm.Solver.from_problem(p)
     assert s.step_kernel == 8
     s.init(*p.fields())
     s.step(3)

@@ -253,14 +253,16 @@ def _patch(f_rows, y_local, x, nx):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_full_size_shear_layer_sampled(orc, lbm, prec):
-    """8192 x 8192 shear layer in the benchmark's launch configuration (float64: the streaming
-    kernel; float32 deviation mode: the TMA-staged tile kernel): after 3 steps, 64 seeded cells
-    of step 4 are recomputed by the oracle from the GPU's step-3 state.  float64: 1e-13 of f.
+    """8192 x 8192 shear layer (float64: the streaming kernel, the float64-pipe kernel of large
+    grids; the automatic double-float kernel has the same check in test_gpu_dd.py; float32
+    deviation mode: the TMA-staged tile kernel of the benchmark's launch configuration): after 3
+    steps, 64 seeded cells of step 4 are recomputed by the oracle from the GPU's step-3 state.
+    float64: 1e-13 of f.
     float32: 1e-6 of f, and per cell 2^-20 (8 float32 ulps) of the cell's largest stored
     deviation |g| = |f - f^eq0| (measured: under 2 ulps).  That is about 1% of the largest
     change of f in the step here, so a dropped or wrong term of the update fails."""
     p = wl.shear_layer(8192)
-    s = lbm.Solver.from_problem(p, precision=prec)
+    s = lbm.Solver.from_problem(p, precision=prec, step_kernel=5 if prec == 0 else 0)
     assert s.step_kernel == (5 if prec == 0 else 2)
     s.init(*p.fields())
     s.step(3)
