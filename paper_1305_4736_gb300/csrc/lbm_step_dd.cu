@@ -9,9 +9,11 @@
 //   split    every staged value becomes hi + lo in place (8 bytes either way);
 //   phase 1  flow velocity and 1/rho on the tile + 1 ring (for grad u);
 //   phase 2  per row: the MRT collision with the energy-flux correction (Eq. 3, Sec. II) in
-//            the shell basis, the limited x and y convection (Sec. III; y slopes from a
-//            sliding window down the thread's column), the forward-Euler update, and one
-//            float64 store per population (the double-float result rounded to float64).
+//            the shell basis, the limited x and y convection (Sec. III; each x face difference
+//            and slope is formed once, by the lane of its column, and passed to the neighbour
+//            lane by a shuffle; y slopes from a sliding window down the thread's column), the
+//            forward-Euler update, and one float64 store per population (the double-float
+//            result rounded to float64).
 // The formulas are those of the float64 kernels, operation for operation; each rounds at
 // about 2^-47 instead of 2^-53, so results agree with the float64 kernels and the oracle to a
 // few parts in 1e14 per step.
@@ -113,24 +115,25 @@ __device__ __forceinline__ void collide_dd(const Coef<dd> &C, const Shells<dd> &
     unbutterfly_diag(S[3], X[3], Y[3], Q[3], out + 12);
 }
 
+__device__ __forceinline__ dd shfl_dd(dd v, int src)
+{
+    return dd{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+__device__ __forceinline__ dd shfl_down_dd(dd v)
+{
+    return dd{__shfl_down_sync(0xffffffffu, v.hi, 1), __shfl_down_sync(0xffffffffu, v.lo, 1)};
+}
+__device__ __forceinline__ dd shfl_up_dd(dd v)
+{
+    return dd{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+
 template <int Lim>
 __device__ __forceinline__ dd slope_dd(dd a, dd b)
 {
     if (Lim == 0) return mc2(a, b);
     if (Lim == 1) return scale2(b, 2.0f);
     return dd{0.0f, 0.0f};
-}
-
-// (F_out - F_in) in upwind order (f_{J-2s}, f_{J-s}, f_J, f_{J+s}), as flux_diff.
-template <int Lim>
-__device__ __forceinline__ dd flux_diff_dd(dd fmm, dd fm, dd f0, dd fp, dd hh)
-{
-    const dd d1 = f0 - fm;
-    if (Lim == 2) return d1;
-    const dd d2 = fp - f0;
-    if (Lim == 1) return d1 + scale2(hh, 2.0f) * (d2 - d1);
-    const dd d0 = fm - fmm;
-    return d1 + hh * (mc2(d1, d2) - mc2(d0, d1));
 }
 
 }  // namespace
@@ -237,6 +240,21 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
         const int r = r0 + k;
         const int gy = y0 + r;
         const dd *p = tile + (r + 2) * S::SW + (lane + S::HX);
+        // values one column outside the warp for the x stencils: lane L < 12 serves the L-th
+        // x-moving population (q = 0, 2, 4, 6, 8 .. 15): D(x0 + 32) for lane 31, and the slope
+        // beyond the warp's upwind end, S(x0 - 1) = mc2(D(x0 - 1), D(x0)) for populations moving
+        // right, S(x0 + 32) = mc2(D(x0 + 32), D(x0 + 33)) for those moving left
+        dd edgeD, edgeS = dd{0.0f, 0.0f};
+        {
+            const int L = lane < 12 ? lane : 0;
+            const int q = L < 4 ? 2 * L : L + 4;
+            const dd *row = tile + q * S::PL + (r + 2) * S::SW;    // smem column = x - x0 + HX
+            edgeD = row[kTmaTX + S::HX] - row[kTmaTX + S::HX - 1];
+            if (Lim == 0) {
+                const int c0 = tsgn_x(q) > 0 ? 0 : kTmaTX + S::HX - 1;
+                edgeS = mc2(row[c0 + 1] - row[c0], row[c0 + 2] - row[c0 + 1]);
+            }
+        }
         dd f[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) f[q] = p[q * S::PL];
@@ -259,8 +277,34 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
             const int shell = q >> 2;
             dd tx = dd{0.0f, 0.0f}, tyv = dd{0.0f, 0.0f};
             if (sx != 0) {
-                const dd *pr = p + q * S::PL;
-                tx = flux_diff_dd<Lim>(pr[-2 * sx], pr[-sx], f[q], pr[sx], C.hh[shell]);
+                // this lane's face difference D(x) = f(x) - f(x-1) and slope S(x) =
+                // mc2(D(x), D(x+1)); the neighbours' values by shuffles, those one column
+                // outside the warp from the duty lane of this population
+                const int duty = q < 8 ? q >> 1 : q - 4;
+                const dd D = f[q] - p[q * S::PL - 1];
+                dd Dr = shfl_down_dd(D);
+                const dd eD = shfl_dd(edgeD, duty);
+                if (lane == kTmaTX - 1) Dr = eD;
+                if (Lim == 2) {
+                    tx = sx > 0 ? D : -Dr;
+                } else if (Lim == 1) {
+                    tx = sx > 0 ? D + scale2(C.hh[shell], 2.0f) * (Dr - D) : (-Dr) + scale2(C.hh[shell], 2.0f) * ((-D) - (-Dr));
+                } else {
+                    const dd Sx = mc2(D, Dr);
+                    const dd eS = shfl_dd(edgeS, duty);
+                    if (sx > 0) {
+                        // upwind slope S(x - 1): from lane - 1, at lane 0 from the duty lane
+                        dd Sl = shfl_up_dd(Sx);
+                        if (lane == 0) Sl = eS;
+                        tx = D + C.hh[shell] * (Sx - Sl);
+                    } else {
+                        // moving left: d1 = -D(x+1), slopes -S(x) and -S(x+1) (mc2 is odd and
+                        // symmetric)
+                        dd Sr = shfl_down_dd(Sx);
+                        if (lane == kTmaTX - 1) Sr = eS;
+                        tx = (-Dr) + C.hh[shell] * ((-Sx) - (-Sr));
+                    }
+                }
             }
             if (sy != 0) {
                 const dd *pc = tile + q * S::PL + (lane + S::HX);
