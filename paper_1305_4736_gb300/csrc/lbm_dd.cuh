@@ -155,11 +155,6 @@ __device__ __forceinline__ dd dd_split(double x)
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const unsigned ex = (hw >> 20) & 0x7FFu;
     const unsigned sign = hw & 0x80000000u;
-    if (ex < 949u) return dd{0.0f, 0.0f};
-    if (ex >= 1150u) {
-        const bool nan = ex == 2047u && ((hw & 0xFFFFFu) | lw) != 0u;
-        return dd{__uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.0f};
-    }
     // top 24 significand bits with the exponent rebiased (1023 -> 127); a carry from the
     // rounding increment moves into the exponent field, as it should
     unsigned fb = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
@@ -167,9 +162,14 @@ __device__ __forceinline__ dd dd_split(double x)
     fb += up;
     // remainder in units of 2^(ex - 1075): the low 29 bits, less 2^29 when hi was rounded up
     const int r = (int)(lw & 0x1FFFFFFFu) - (int)(up << 29);
-    const float scale = __uint_as_float((ex - 948u) << 23);   // 2^(ex - 1075), a normal float
+    const float scale = __uint_as_float(((ex - 948u) & 0xFFu) << 23);   // 2^(ex - 1075) in range
     const float lo = __fmul_rn(__int2float_rn(r), scale);
-    return dd{__uint_as_float(fb | sign), __uint_as_float(__float_as_uint(lo) ^ sign)};
+    // selects, not branches: flushed, overflowing and non-finite inputs
+    const bool tiny = ex < 949u, big = ex >= 1150u;
+    const bool nan = ex == 2047u && ((hw & 0xFFFFFu) | lw) != 0u;
+    const unsigned hbits = big ? (sign | 0x7F800000u | (nan ? 0x400000u : 0u)) : (fb | sign);
+    return dd{tiny ? 0.0f : __uint_as_float(hbits),
+              (tiny || big) ? 0.0f : __uint_as_float(__float_as_uint(lo) ^ sign)};
 }
 
 // hi + lo rounded to float64, after renormalising the pair.  The sum is exact in float64
@@ -179,45 +179,30 @@ __device__ __forceinline__ dd dd_split(double x)
 __device__ __forceinline__ double dd_to_double(dd v)
 {
     v = fast2sum(v.hi, v.lo);
-    unsigned hb = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
-    unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
-    if (eh == 0u) {   // hi is zero (or subnormal): the value is lo
-        hb = lb;
-        eh = el;
-        el = 0u;
-        if (eh == 0u) return __longlong_as_double((long long)((unsigned long long)(hb & 0x80000000u) << 32));
-    }
-    if (eh == 0xFFu) {   // inf / NaN: keep it non-finite
-        return __longlong_as_double((long long)(((unsigned long long)(hb & 0x80000000u) << 32) |
-                                                0x7FF8000000000000ull));
-    }
+    const unsigned hb0 = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
+    const unsigned eh0 = (hb0 >> 23) & 0xFFu, el0 = (lb >> 23) & 0xFFu;
+    // hi zero (or subnormal): the value is lo
+    const bool hz = eh0 == 0u;
+    const unsigned hb = hz ? lb : hb0, eh = hz ? el0 : eh0, el = hz ? 0u : el0;
     // significands with the implicit bit, in units of hi's float64 ulp: hi -> 24 bits << 29
-    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    const unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+    const int sh = 29 - ((int)eh - (int)el);            // <= 5 for a normalised pair
+    const int rs = min(max(-sh, 1), 63);                 // right shift when sh < 0
+    const unsigned long long cl = ml << max(sh, 0);
+    const unsigned long long cr = rs < 40 ? (ml + (1ull << (rs - 1))) >> rs : 0ull;   // rounded half up
+    const unsigned long long c = el == 0u ? 0ull : (sh >= 0 ? cl : cr);
+    const bool opp = ((hb ^ lb) & 0x80000000u) != 0u && el != 0u;
+    unsigned long long S = opp ? M - c : M + c;
     int e = (int)eh;
-    if (el != 0u) {
-        const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
-        const int k = (int)eh - (int)el;                      // >= 24 for a normalised pair
-        unsigned long long c;
-        if (k <= 29) c = ml << (29 - k);
-        else if (k - 29 < 40) c = (ml + (1ull << (k - 30))) >> (k - 29);
-        else c = 0ull;
-        if ((hb ^ lb) & 0x80000000u) {
-            M -= c;
-            if (M < (1ull << 52)) {   // hi was a power of two: one bit of normalisation
-                M <<= 1;
-                e -= 1;
-            }
-        } else {
-            M += c;
-            if (M >= (1ull << 53)) {  // not reached by a normalised pair; kept for safety
-                M = (M + 1ull) >> 1;
-                e += 1;
-            }
-        }
-    }
-    const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
-                                    ((unsigned long long)(e + 896) << 52) | (M & ((1ull << 52) - 1ull));
-    return __longlong_as_double((long long)bits);
+    const bool down = opp && S < (1ull << 52);           // hi was a power of two
+    const bool upn = !opp && S >= (1ull << 53);          // not reached by a normalised pair
+    S = down ? S << 1 : (upn ? (S + 1ull) >> 1 : S);
+    e += down ? -1 : (upn ? 1 : 0);
+    const unsigned long long sgn = (unsigned long long)(hb & 0x80000000u) << 32;
+    const unsigned long long bits = sgn | ((unsigned long long)(e + 896) << 52) | (S & ((1ull << 52) - 1ull));
+    const unsigned long long out = eh == 0u ? sgn : (eh == 0xFFu ? (sgn | 0x7FF8000000000000ull) : bits);
+    return __longlong_as_double((long long)out);
 }
 
 }  // namespace lbm
