@@ -62,7 +62,14 @@ TRAFFIC_PER_CELL = {
             "sha": "4d6d8aaddb3ad2e2"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "1fae702a20fe4afb"},
+    "dd": {"bytes": None, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": None},
 }
+# float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
+# float64 kernel, counted by ncu on the same sources (profiles/k_step_dd_f64_shear_layer.md);
+# None when the sources changed since.
+DD_FP32_OPS = {"ops": None, "sha": None}
+FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 
 def kernel_sources_sha(names) -> str:
@@ -78,10 +85,18 @@ def traffic_per_launch(mode: str, cells: int, kernel: str):
     """ncu DRAM bytes of one fused-step launch scaled to `cells`, or None when the captured
     kernel is not the one that ran or its sources changed since the capture."""
     t = TRAFFIC_PER_CELL.get(mode)
-    want = "k_step_tma<" if mode == "f32" else "k_step_stream<"
-    if not t or not kernel.startswith(want) or kernel_sources_sha(t["sources"]) != t["sha"]:
+    want = {"f32": "k_step_tma<", "f64": "k_step_stream<", "dd": "k_step_dd<"}[mode]
+    if not t or not t["bytes"] or not kernel.startswith(want) or kernel_sources_sha(t["sources"]) != t["sha"]:
         return None
     return t["bytes"] * cells
+
+
+def dd_fp32_ops_per_cell():
+    """ncu's float32-pipe operations per cell of the double-float kernel, while its sources
+    still hash to the captured value."""
+    if not DD_FP32_OPS["ops"] or kernel_sources_sha(TRAFFIC_PER_CELL["dd"]["sources"]) != DD_FP32_OPS["sha"]:
+        return None
+    return DD_FP32_OPS["ops"]
 
 
 def parse_args(argv=None):
@@ -376,22 +391,49 @@ def fp64_line(lbm, p, args, device, world, hbm):
         r64 = run_mode(lbm, p, lbm.LBM_FP64, k64, args.warmup, device, world, args.step_kernel)
     ops = FP64_OPS_PER_CELL * cells / (r64["step_kernel_ms"] * 1e-3)
     peak_ops = peak64 / 2.0
+    hbm_frac = BYTES_PER_CELL["f64"] * cells / (r64["step_kernel_ms"] * 1e-3) / 1e9 / hbm
+    clocks = clk64.summary()
+    if r64["kernel"].startswith("k_step_dd"):
+        # double-float arithmetic on the float32 pipe: its peak from the unit counts and the
+        # sampled SM clock, the executed float32 operations per cell from ncu
+        import torch
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak32 = sms * FP32_LANES_PER_SM * mhz * 1e6
+        per_cell = dd_fp32_ops_per_cell()
+        ach = per_cell * cells / (r64["step_kernel_ms"] * 1e-3) if per_cell else None
+        roof = {"bound": "alu", "achieved": ach / 1e12 if ach else None, "peak": peak32 / 1e12,
+                "unit": "T fp32-op/s", "frac": ach / peak32 if ach else None,
+                "traffic": traffic_per_launch("dd", cells, r64["kernel"]),
+                "kernel": r64["kernel"], "kernel_ms": r64["step_kernel_ms"],
+                "fp32_ops_per_cell": per_cell,
+                "fp32_ops_source": "ncu float32 add + multiply + FMA thread instructions per cell of this kernel",
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} float32 lanes x sampled SM clock {mhz:.0f} MHz",
+                "fp64_pipe_equivalent": {"algorithmic_fp64_ops_per_cell": FP64_OPS_PER_CELL,
+                                         "achieved": ops / 1e12, "fp64_fma_chain_rate": peak_ops / 1e12,
+                                         "ratio": ops / peak_ops},
+                "hbm_frac": hbm_frac}
+    else:
+        roof = {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
+                "unit": "T fp64-op/s", "frac": ops / peak_ops,
+                "traffic": traffic_per_launch("f64", cells, r64["kernel"]),
+                "kernel": r64["kernel"], "kernel_ms": r64["step_kernel_ms"],
+                "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
+                "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
+                "hbm_frac": hbm_frac}
     return {
         "metric": METRIC, "value": world * cells * k64 / (r64["ms"] * 1e-3), "unit": UNIT, "steps": k64,
-        "warmup": args.warmup, "n_gpus": world, "ms_per_step": r64["ms"] / k64, "dtype": "f64",
+        "warmup": args.warmup, "n_gpus": world, "ms_per_step": r64["ms"] / k64,
+        "dtype": "df64" if r64["kernel"].startswith("k_step_dd") else "f64",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
         "config": {"workload": f"shear_layer_{p.nx}x{p.ny}", "mode": "FP64 (f stored in float64)",
+                   "arithmetic": ("double-float (pairs of float32) on the float32 pipe"
+                                  if r64["kernel"].startswith("k_step_dd") else "float64"),
                    "grid": [p.nx, p.ny], "l2": "inputs larger than L2 (8.6 GB per population buffer)"},
-        "roofline": {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "T fp64-op/s", "frac": ops / peak_ops,
-                     "traffic": traffic_per_launch("f64", cells, r64["kernel"]),
-                     "kernel": r64["kernel"], "kernel_ms": r64["step_kernel_ms"],
-                     "algorithmic_ops_per_cell": FP64_OPS_PER_CELL,
-                     "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64), one op per FMA",
-                     "hbm_frac": BYTES_PER_CELL["f64"] * cells / (r64["step_kernel_ms"] * 1e-3) / 1e9 / hbm},
+        "roofline": roof,
         "e2e": {"value": world * cells * k64 / r64["e2e_s"], "unit": UNIT,
                 "h2d_bytes_per_step": 4 * 8 * cells / k64, "d2h_bytes_per_step": 4 * 8 * cells / k64},
-        "gpu_launches": r64["launches"], "clocks": clk64.summary(),
+        "gpu_launches": r64["launches"], "clocks": clocks,
         "kernel_ms": {"step": r64["step_kernel_ms"], "ghost": r64["ghost_ms"]},
         "totals_drift": r64["totals_drift"],
     }
@@ -441,9 +483,9 @@ def serving_measure(count, steps, max_nx, max_ny, device, seed=1305):
 
 
 def batch_measure(device, steps=20, warmup=3, seed=1305):
-    """Batched stepping (one lbm_batch: a ghost launch and a fused-step launch per step over a
-    tile list of all grids) of 24 uneven float32 shear-layer grids whose buffers exceed L2,
-    against stepping the same grids one at a time on their automatic kernels."""
+    """Batched stepping (one lbm_batch: a ghost launch and one batched tile-kernel launch per
+    step over the tiles of all grids) of 24 uneven float32 shear-layer grids whose buffers
+    exceed L2, against stepping the same grids one at a time on their automatic kernels."""
     import numpy as np
     import torch
     from paper_1305_4736_gb300 import lbm, workloads as wl
@@ -487,8 +529,8 @@ def batch_measure(device, steps=20, warmup=3, seed=1305):
             "ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                          "peak_source": f"{peak_src} hbm_gbs", "traffic": None,
-                         "kernel": "k_ghost_batch, then each grid's k_step_tma<float,dev,MC> on 8 forked "
-                                   "streams (grids under 512 cells per SM: k_step_batch), in one CUDA graph"},
+                         "kernel": "k_ghost_batch, then k_step_tma_batch<MC> over the tiles of all 24 grids "
+                                   "(one CTA per 32 x 16 tile), in one CUDA graph"},
             "one_at_a_time_ms_per_step": ms_solo, "speedup_vs_one_at_a_time": ms_solo / ms}
 
 
@@ -537,10 +579,21 @@ def config_gpu(lbm, p, precision, steps, warmup, device, hbm, peak_ops=None):
                            "peak_source": "measured hbm_gbs"}
     elif peak_ops:
         ops = FP64_OPS_PER_CELL * cells / (k_ms * 1e-3)
-        out["roofline"] = {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
-                           "unit": "T fp64-op/s", "frac": ops / peak_ops,
-                           "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64)",
-                           "hbm_frac": BYTES_PER_CELL["f64"] * cells / (k_ms * 1e-3) / 1e9 / hbm}
+        hbm_frac = BYTES_PER_CELL["f64"] * cells / (k_ms * 1e-3) / 1e9 / hbm
+        if kern.startswith("k_step_dd"):
+            import torch
+            sms = torch.cuda.get_device_properties(device).multi_processor_count
+            peak32 = sms * FP32_LANES_PER_SM * 2070.0 * 1e6
+            per_cell = dd_fp32_ops_per_cell()
+            ach = per_cell * cells / (k_ms * 1e-3) if per_cell else None
+            out["roofline"] = {"bound": "alu", "achieved": ach / 1e12 if ach else None, "peak": peak32 / 1e12,
+                               "unit": "T fp32-op/s", "frac": ach / peak32 if ach else None,
+                               "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} float32 lanes x 2070 MHz",
+                               "fp64_pipe_equivalent_ratio": ops / peak_ops, "hbm_frac": hbm_frac}
+        else:
+            out["roofline"] = {"bound": "alu", "achieved": ops / 1e12, "peak": peak_ops / 1e12,
+                               "unit": "T fp64-op/s", "frac": ops / peak_ops,
+                               "peak_source": "measured fp64 FMA-chain rate (lbm_peak_fp64)", "hbm_frac": hbm_frac}
     return out
 
 
@@ -652,6 +705,7 @@ def precision_study(lbm, p, device, steps, every=None, delta_every=None, periodi
     dbufs = {prec: pinned_like(np.zeros((16, p.ny, p.nx))) for prec in sol} if delta_every else None
     worst = {"rho": {"l1": 0.0, "max": 0.0}, "u": {"l1": 0.0, "max": 0.0}, "T": {"l1": 0.0, "max": 0.0}}
     dworst = 0.0
+    series = []
     done = 0
     tstart = time.perf_counter()
     while done < steps:
@@ -669,6 +723,8 @@ def precision_study(lbm, p, device, steps, every=None, delta_every=None, periodi
                 raise RuntimeError(f"lbm_moments failed ({rc}) at step {done}")
             m[prec] = [x[0] for x in f]
         e = field_errors(m[lbm.LBM_FP32_DEV], m[lbm.LBM_FP64])
+        if done % 500 == 0 or done == steps:
+            series.append({"step": done, **{k: {"l1": e[k]["l1"], "max": e[k]["max"]} for k in ("rho", "u", "T")}})
         for k in worst:
             for q in ("l1", "max"):
                 worst[k][q] = max(worst[k][q], e[k][q])
@@ -680,6 +736,7 @@ def precision_study(lbm, p, device, steps, every=None, delta_every=None, periodi
         sv.close()
     a, b = t1[lbm.LBM_FP32_DEV], t1[lbm.LBM_FP64]
     out = {"steps": steps, "final": e, "worst_over_checkpoints": worst, "checkpoint_every": every,
+           "series_every_500": series,
            "totals_fp32_vs_fp64": {"mass": abs(a[0] - b[0]) / abs(b[0]), "momentum_x": abs(a[1] - b[1]) / abs(b[0]),
                                    "momentum_y": abs(a[2] - b[2]) / abs(b[0]), "energy": abs(a[3] - b[3]) / abs(b[3])},
            "budget": {"l1": 1e-4, "max": 1e-3, "totals_drift": 1e-6},

@@ -1005,6 +1005,7 @@ struct lbm_batch {
         int prec = 0, limiter = 0;
         std::vector<int> members;               // indices into ctxs
         std::vector<char> own;                   // member steps on its own kernel (no tiles)
+        std::vector<char> tma;                   // member's tiles go to the batched TMA-staged kernel
         std::vector<lbm::BatchGrid> hG;
         void *block = nullptr;                   // device: Params[n] | BatchGrid[n] | int4[ntiles]
         size_t bytes = 0;
@@ -1013,13 +1014,20 @@ struct lbm_batch {
         int4 *dT = nullptr;
         int ntiles = 0, max_ghost = 0;
         int nt = lbm::kBatchThreads;             // threads (= cells) per tile
+        // batched TMA-staged kernel: CUtensorMap[2n] | Coef<dd>[n] (float64) | int4[ntt]
+        void *tblock = nullptr;
+        size_t tbytes = 0;
+        CUtensorMap *dM = nullptr;
+        lbm::Coef<lbm::dd> *dC = nullptr;
+        int4 *dTT = nullptr;
+        int ntt = 0;
     };
     std::vector<lbm_ctx *> ctxs;
     std::vector<Group> groups;
-    // contexts large enough for their own TMA-staged kernel (one wave of its tiles): their
-    // ghost cells come from their group's batched ghost launch, their step from that kernel,
-    // launched on kForks forked streams so that the grids' kernels overlap; their buffer parity
-    // at capture time
+    // contexts on the streaming or the double-buffered kernel with at least a quarter wave of
+    // its work: their ghost cells come from their group's batched ghost launch, their step from
+    // that kernel, launched on kForks forked streams so that the grids' kernels overlap; their
+    // buffer parity at capture time
     static constexpr int kForks = 8;
     std::vector<int> solo, solo_cur;
     cudaStream_t fork[kForks] = {};
@@ -1059,6 +1067,10 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
     for (auto &g : b->groups) {
         ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
                                     g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
+        if (ce == cudaSuccess && g.ntt > 0)
+            ce = g.prec == LBM_FP64
+                     ? lbm::launch_step_dd_batch(g.dP, g.dC, g.dG, g.dM, g.dTT, g.ntt, g.limiter, phase, st)
+                     : lbm::launch_step_tma_batch(g.dP, g.dG, g.dM, g.dTT, g.ntt, g.limiter, phase, st);
         if (ce != cudaSuccess) return ce;
     }
     for (size_t j = 0; j < b->solo.size(); j++) {
@@ -1073,13 +1085,19 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
     return ce;
 }
 
-// A context runs its own TMA-staged kernel inside the batch when it has one and fills at
-// least a quarter of a wave of that kernel's tiles (512 cells per SM; the forked streams let
-// several such kernels share the SMs); smaller grids share the packed tile kernel, where one
-// launch serves them all.
+// Inside a batch, a context whose kernel is the TMA-staged tile kernel (float32) or the
+// double-float kernel (float64) has its tiles in the group's batched TMA-staged launch, which
+// serves grids of every size; a context on the streaming or the double-buffered kernel runs its
+// own kernel when it fills at least a quarter of a wave (512 cells per SM; forked streams let
+// several such kernels share the SMs); the other grids share the packed plain tile kernel.
+bool batch_tma(const lbm_ctx *c)
+{
+    return (c->prec == LBM_FP32_DEV && c->use_tma) || (c->prec == LBM_FP64 && c->use_dd);
+}
+
 bool batch_solo(const lbm_ctx *c, int sms)
 {
-    return (c->use_tma || c->use_stream || c->use_pipe || c->use_dd) && (long long)c->P.nx * c->P.ny >= 512LL * sms;
+    return (c->use_stream || c->use_pipe) && (long long)c->P.nx * c->P.ny >= 512LL * sms;
 }
 
 }  // namespace
@@ -1111,7 +1129,8 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
     b->ctas = 4 * sms;
     for (int i = 0; i < n; i++) {
         const lbm_ctx *c = ctxs[i];
-        const bool own = batch_solo(c, sms);
+        const bool tma = batch_tma(c);
+        const bool own = !tma && batch_solo(c, sms);
         if (own) b->solo.push_back(i);
         lbm_batch::Group *g = nullptr;
         for (auto &gg : b->groups)
@@ -1124,6 +1143,7 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
         }
         g->members.push_back(i);
         g->own.push_back(own ? 1 : 0);
+        g->tma.push_back(tma ? 1 : 0);
     }
     for (auto &g : b->groups) {
         // float64 groups too small to give every SM four 256-cell tiles take 64-cell tiles,
@@ -1131,16 +1151,29 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
         if (g.prec == LBM_FP64) {
             long long cells = 0;
             for (size_t k = 0; k < g.members.size(); k++)
-                if (!g.own[k]) cells += (long long)b->ctxs[g.members[k]]->P.nx * b->ctxs[g.members[k]]->P.ny;
+                if (!g.own[k] && !g.tma[k]) cells += (long long)b->ctxs[g.members[k]]->P.nx * b->ctxs[g.members[k]]->P.ny;
             g.nt = cells >= 4LL * lbm::kBatchThreads * sms ? lbm::kBatchThreads : lbm::kBatchThreadsFp64;
         }
-        std::vector<int4> tiles;
+        std::vector<int4> tiles, ttiles;
         std::vector<lbm::Params> hp;
+        std::vector<CUtensorMap> hm;
+        std::vector<lbm::Coef<lbm::dd>> hc;
+        const int tr = g.prec == LBM_FP64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR;
         for (size_t k = 0; k < g.members.size(); k++) {
             const lbm_ctx *c = b->ctxs[g.members[k]];
             hp.push_back(c->P);
-            g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->cur, 0});
+            hp.back().wrap = 0;                      // the batched ghost fill writes every ghost cell
+            g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->tma_err, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
+            CUtensorMap none{};
+            hm.push_back(g.tma[k] ? c->tmap[0] : none);
+            hm.push_back(g.tma[k] ? c->tmap[1] : none);
+            if (g.prec == LBM_FP64) hc.push_back(c->cdd);
+            if (g.tma[k]) {
+                for (int y = 0; y < c->P.ny; y += tr)
+                    for (int x = 0; x < c->P.nx; x += lbm::kTmaTX) ttiles.push_back(make_int4((int)k, x, y, 0));
+                continue;
+            }
             if (g.own[k]) continue;                  // ghost cells only
             const int lt = lbm::plain_log_tx(c->P.nx);
             const int nt = g.nt;
@@ -1164,6 +1197,23 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             ce = cudaMemcpyAsync(g.dG, g.hG.data(), g.hG.size() * sizeof(lbm::BatchGrid), cudaMemcpyHostToDevice,
                                  b->stream);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(g.dT, tiles.data(), nt, cudaMemcpyHostToDevice, b->stream);
+        g.ntt = (int)ttiles.size();
+        if (ce == cudaSuccess && g.ntt > 0) {
+            const size_t nm = up(hm.size() * sizeof(CUtensorMap)), nc = up(hc.size() * sizeof(lbm::Coef<lbm::dd>));
+            g.tbytes = nm + nc + ttiles.size() * sizeof(int4);
+            g.tblock = b->alloc.alloc(g.tbytes, b->stream, b->alloc.user);
+            if (!g.tblock) { cudaGetLastError(); lbm_batch_destroy(b); return fail(nullptr, LBM_ERR_OOM, "batch tables"); }
+            g.dM = (CUtensorMap *)g.tblock;
+            g.dC = (lbm::Coef<lbm::dd> *)((char *)g.tblock + nm);
+            g.dTT = (int4 *)((char *)g.tblock + nm + nc);
+            ce = cudaMemcpyAsync(g.dM, hm.data(), hm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, b->stream);
+            if (ce == cudaSuccess && !hc.empty())
+                ce = cudaMemcpyAsync(g.dC, hc.data(), hc.size() * sizeof(lbm::Coef<lbm::dd>), cudaMemcpyHostToDevice,
+                                     b->stream);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(g.dTT, ttiles.data(), ttiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                     b->stream);
+        }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
         if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "batch tables"); }
     }
@@ -1241,8 +1291,10 @@ void lbm_batch_destroy(lbm_batch *b)
         if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    for (auto &g : b->groups)
+    for (auto &g : b->groups) {
         if (g.block && b->alloc.free) b->alloc.free(g.block, g.bytes, b->stream, b->alloc.user);
+        if (g.tblock && b->alloc.free) b->alloc.free(g.tblock, g.tbytes, b->stream, b->alloc.user);
+    }
     delete b;
 }
 

@@ -32,9 +32,11 @@ int plain_log_tx(int nx);
 constexpr int kBatchThreads = kTX * kTY;
 constexpr int kBatchThreadsFp64 = 64;
 
-// One grid of a batch: its two population buffers and which one holds the current step.
+// One grid of a batch: its two population buffers, which one holds the current step, and the
+// flag its TMA-fed kernels raise when a copy wait runs out.
 struct BatchGrid {
     void *buf[2];
+    int *err;
     int cur;
     int pad;
 };
@@ -77,6 +79,14 @@ struct TmaShape {
     static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * (sizeof(R) == sizeof(float) ? 2 : 3) * UW * UH;
 };
 bool tma_supported(const Params &P, int prec);
+// Batched TMA-staged steps: one CTA per tile of a list {grid, x0, y0, 0} spanning the grids of a
+// batch group (tiles of TmaShape<R>); `maps` holds two tensor maps per grid (buffer 0, buffer
+// 1), `phase` as launch_step_batch.  float32 (the tile kernel) and float64 in double-float
+// arithmetic (`coefs`: one Coef<dd> per grid).
+cudaError_t launch_step_tma_batch(const Params *Pall, const BatchGrid *G, const void *maps, const int4 *tiles,
+                                  int ntiles, int limiter, int phase, cudaStream_t st);
+cudaError_t launch_step_dd_batch(const Params *Pall, const void *coefs, const BatchGrid *G, const void *maps,
+                                 const int4 *tiles, int ntiles, int limiter, int phase, cudaStream_t st);
 // Failure-path check of the bounded mbarrier waits (lbm_wait_selftest): *flag = 1 when the
 // wait on a phase that nothing completes gave up at its limit; *ms = the kernel's duration.
 cudaError_t wait_selftest(int *flag, float *ms);

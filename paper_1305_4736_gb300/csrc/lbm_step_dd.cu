@@ -139,56 +139,22 @@ __device__ __forceinline__ dd slope_dd(dd a, dd b)
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// The kernel.  Shape as the float64 TMA-staged kernel: 8 warps, 32 x 32 tiles, 4 rows per
-// thread, one CTA per SM (the staged tile takes 162 KB).
+// The tile body shared by the single-grid and the batched kernel: the staged float64 tile in
+// shared memory (smraw) is split, then phases 1 and 2 produce the tile's new float64 values.
 // ---------------------------------------------------------------------------
-template <int Lim, bool Wrap, bool C9>
-__global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
-k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, const __grid_constant__ CUtensorMap tm,
-          const double *__restrict__ fin, double *__restrict__ fout, int *err)
+template <int Lim, bool C9>
+__device__ __forceinline__ void dd_tile(const Params &P, const Coef<dd> &C, unsigned char *smraw,
+                                        double *__restrict__ fout, int x0, int y0)
 {
     using S = TmaShape<double>;
-    extern __shared__ __align__(128) unsigned char smraw[];
     double *tile64 = reinterpret_cast<double *>(smraw);
     dd *tile = reinterpret_cast<dd *>(smraw);
     dd *su = tile + NQ * S::PL;
     dd *sv = su + S::UW * S::UH;
     dd *sir = sv + S::UW * S::UH;
-    __shared__ __align__(8) unsigned long long bar;
-
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
     constexpr int kThreads = kTmaTX * S::TT;
     const int nx = P.nx, ny = P.ny;
-    const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * S::TR;
-    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // box origin: interior column x0 - HX = padded column x0 + OX - HX; interior row y0 - 2 =
-        // padded row y0
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(tile64);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
-                     "r"((unsigned)S::tile_bytes) : "memory");
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 + OX - S::HX), "r"(y0),
-                     "r"(0), "r"(bar_a) : "memory");
-    }
-    const bool ok = mbar_wait(bar_a, 0);
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
-        }
-        return;
-    }
-    if (Wrap && (x0 < S::HX || x0 + kTmaTX + S::HX > nx)) {
-        wrap_halo<double>(P, fin, tile64, x0, y0, tid, kThreads);
-        __syncthreads();
-    }
     // ---- split: float64 -> hi + lo in place
     for (int k = tid; k < NQ * S::PL; k += kThreads) tile[k] = dd_split(tile64[k]);
     __syncthreads();
@@ -332,6 +298,115 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The single-grid kernel.  Shape as the float64 TMA-staged kernel: 8 warps, 32 x 32 tiles,
+// 4 rows per thread, one CTA per SM (the staged tile takes 162 KB).
+// ---------------------------------------------------------------------------
+template <int Lim, bool Wrap, bool C9>
+__global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
+k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, const __grid_constant__ CUtensorMap tm,
+          const double *__restrict__ fin, double *__restrict__ fout, int *err)
+{
+    using S = TmaShape<double>;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    double *tile64 = reinterpret_cast<double *>(smraw);
+    __shared__ __align__(8) unsigned long long bar;
+
+    const int tid = threadIdx.y * kTmaTX + threadIdx.x;
+    constexpr int kThreads = kTmaTX * S::TT;
+    const int nx = P.nx;
+    const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * S::TR;
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // box origin: interior column x0 - HX = padded column x0 + OX - HX; interior row y0 - 2 =
+        // padded row y0
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(tile64);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"((unsigned)S::tile_bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(x0 + OX - S::HX), "r"(y0),
+                     "r"(0), "r"(bar_a) : "memory");
+    }
+    const bool ok = mbar_wait(bar_a, 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
+        }
+        return;
+    }
+    if (Wrap && (x0 < S::HX || x0 + kTmaTX + S::HX > nx)) {
+        wrap_halo<double>(P, fin, tile64, x0, y0, tid, kThreads);
+        __syncthreads();
+    }
+    dd_tile<Lim, C9>(P, C, smraw, fout, x0, y0);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: one CTA per tile of a list spanning the grids of a batch group.  A tile
+// {grid, x0, y0} names its grid: the CTA copies that grid's parameter block and double-float
+// coefficients into shared memory and issues its tile copy with the grid's tensor map from
+// global memory.  The ghost cells come from the batched ghost fill, so no x wrap.  The
+// energy-flux correction runs for every grid; its factors are zero where s8 = s5, which leaves
+// the residuals unchanged bit for bit.
+// ---------------------------------------------------------------------------
+template <int Lim>
+__global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
+k_step_dd_batch(const Params *__restrict__ Pall, const Coef<dd> *__restrict__ Call, const BatchGrid *__restrict__ G,
+                const CUtensorMap *__restrict__ maps, const int4 *__restrict__ tiles, int phase)
+{
+    using S = TmaShape<double>;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(16) Params Ps;
+    __shared__ __align__(16) Coef<dd> Cs;
+    __shared__ __align__(8) unsigned long long bar;
+    const int tid = threadIdx.y * kTmaTX + threadIdx.x;
+    constexpr int kThreads = kTmaTX * S::TT;
+    const int4 t = tiles[blockIdx.x];
+    const BatchGrid g = G[t.x];
+    const int in = g.cur ^ phase;
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const CUtensorMap *tm = maps + 2 * t.x + in;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(smraw);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"((unsigned)S::tile_bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(t.y + OX - S::HX), "r"(t.z),
+                     "r"(0), "r"(bar_a) : "memory");
+    }
+    // the grid's parameter block and coefficients, while the tile copy is in flight
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(Pall + t.x);
+        int4 *dst = reinterpret_cast<int4 *>(&Ps);
+        for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kThreads) dst[k] = src[k];
+        const int4 *srcc = reinterpret_cast<const int4 *>(Call + t.x);
+        int4 *dstc = reinterpret_cast<int4 *>(&Cs);
+        for (int k = tid; k < (int)(sizeof(Coef<dd>) / sizeof(int4)); k += kThreads) dstc[k] = srcc[k];
+    }
+    const bool ok = mbar_wait(bar_a, 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicExch(g.err, 1);
+            mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
+        }
+        return;
+    }
+    dd_tile<Lim, true>(Ps, Cs, smraw, static_cast<double *>(g.buf[in ^ 1]), t.y, t.z);
+}
+
 // Coefficients in double-float from the float64 tables (host).
 void coef_dd(const Params &P, Coef<dd> *out)
 {
@@ -373,6 +448,20 @@ cudaError_t launch_step_dd(const Params &P, const void *coef, const void *tmap, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_step_dd_batch(const Params *Pall, const void *coefs, const BatchGrid *G, const void *maps,
+                                 const int4 *tiles, int ntiles, int limiter, int phase, cudaStream_t st)
+{
+    using S = TmaShape<double>;
+    if (ntiles <= 0) return cudaSuccess;
+    const dim3 block(kTmaTX, S::TT);
+    const Coef<dd> *C = static_cast<const Coef<dd> *>(coefs);
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    if (limiter == 0) k_step_dd_batch<0><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
+    else if (limiter == 1) k_step_dd_batch<1><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
+    else k_step_dd_batch<2><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
+    return cudaGetLastError();
+}
+
 cudaError_t dd_prepare()
 {
     cudaError_t e = cudaSuccess;
@@ -392,6 +481,9 @@ cudaError_t dd_prepare()
     set((const void *)k_step_dd<2, false, true>);
     set((const void *)k_step_dd<2, true, false>);
     set((const void *)k_step_dd<2, true, true>);
+    set((const void *)k_step_dd_batch<0>);
+    set((const void *)k_step_dd_batch<1>);
+    set((const void *)k_step_dd_batch<2>);
     return e;
 }
 

@@ -109,6 +109,38 @@ __device__ __forceinline__ void phase2_packed(const Params &P, const float2 *til
     }
 }
 
+// Phase 1 of the tile kernels: flow velocity and 1/rho on the tile plus its ring.  Cells of the
+// ring outside the domain's cross (corners, beyond the ghost layer) get values that only lanes
+// whose results are not stored read.
+template <typename R, bool Dev>
+__device__ __forceinline__ void flow_phase(const Coef<R> &C, const R *tile, R *su, R *sv, R *sir, int tid)
+{
+    using S = TmaShape<R>;
+    constexpr int kStep = kTmaTX * S::TT;
+    int i = tid % S::UW, j = tid / S::UW;
+    for (int k = tid; k < S::UW * S::UH; k += kStep) {
+        R ux, uy, ir;
+        if constexpr (sizeof(R) == sizeof(float))
+            flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux,
+                         uy, ir);
+        else
+            flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux, uy, ir);
+        i += kStep % S::UW;
+        j += kStep / S::UW;
+        if (i >= S::UW) {
+            i -= S::UW;
+            j++;
+        }
+        if constexpr (sizeof(R) == sizeof(float)) {
+            reinterpret_cast<float2 *>(su)[k] = f2(ux, uy);   // float32: (u_x, u_y) pairs
+        } else {
+            su[k] = ux;
+            sv[k] = uy;
+            sir[k] = ir;
+        }
+    }
+}
+
 // Wrap: the grid's x halo is wrapped in the kernel (P.wrap bit 0); a separate instantiation,
 // so that the other grids run a kernel without that branch.
 template <typename R, bool Dev, int Lim, bool Wrap>
@@ -171,32 +203,8 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         __syncthreads();
     }
     const Coef<R> &C = coef<R>(P);
-    // ---- phase 1: flow velocity and 1/rho on the tile plus its ring.  Cells of the ring
-    // outside the domain's cross (corners, beyond the ghost layer) get values that only
-    // lanes whose results are not stored read.
-    constexpr int kStep = kTmaTX * S::TT;
-    int i = tid % S::UW, j = tid / S::UW;
-    for (int k = tid; k < S::UW * S::UH; k += kStep) {
-        R ux, uy, ir;
-        if constexpr (sizeof(R) == sizeof(float))
-            flow_at<Dev>(C, reinterpret_cast<const float2 *>(tile) + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux,
-                         uy, ir);
-        else
-            flow_at<Dev>(C, tile + (j + 1) * S::SW + (i + S::HX - 1), S::PL, ux, uy, ir);
-        i += kStep % S::UW;
-        j += kStep / S::UW;
-        if (i >= S::UW) {
-            i -= S::UW;
-            j++;
-        }
-        if constexpr (sizeof(R) == sizeof(float)) {
-            reinterpret_cast<float2 *>(su)[k] = f2(ux, uy);   // float32: (u_x, u_y) pairs
-        } else {
-            su[k] = ux;
-            sv[k] = uy;
-            sir[k] = ir;
-        }
-    }
+    // ---- phase 1: flow velocity and 1/rho on the tile plus its ring
+    flow_phase<R, Dev>(C, tile, su, sv, sir, tid);
     __syncthreads();
 
     // ---- phase 2: rows ty*KR .. ty*KR+KR-1 of the tile, column `lane`
@@ -296,6 +304,89 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
         }
 
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form (float32): one CTA per tile of a list spanning the grids of a batch group.  A
+// tile {grid, x0, y0} names its grid: the CTA copies that grid's parameter block into shared
+// memory and issues its tile copy with the grid's tensor map from global memory; the
+// arithmetic is that of k_step_tma.  The ghost cells come from the batched ghost fill, so no
+// x wrap.  The L2 prefetch goes to the tile half a resident wave further down the list.
+// ---------------------------------------------------------------------------
+template <int Lim>
+__global__ void __launch_bounds__(kTmaTX * TmaShape<float>::TT, TmaShape<float>::CTAS)
+k_step_tma_batch(const Params *__restrict__ Pall, const BatchGrid *__restrict__ G, const CUtensorMap *__restrict__ maps,
+                 const int4 *__restrict__ tiles, int ntiles, int phase)
+{
+    using S = TmaShape<float>;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float *tile = reinterpret_cast<float *>(smraw);
+    float *su = tile + NQ * S::PL;
+    __shared__ __align__(16) Params Ps;
+    __shared__ __align__(8) unsigned long long bar;
+
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
+    constexpr int kThreads = kTmaTX * S::TT;
+    const int4 t = tiles[blockIdx.x];
+    const BatchGrid g = G[t.x];
+    const int in = g.cur ^ phase;
+    const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const CUtensorMap *tm = maps + 2 * t.x + in;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(tile);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"((unsigned)S::tile_bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(t.y + OX - S::HX), "r"(t.z),
+                     "r"(0), "r"(bar_a) : "memory");
+        unsigned nsm;
+        asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+        const long long bn = (long long)blockIdx.x + (long long)S::CTAS * nsm / 2;
+        if (bn < ntiles) {
+            const int4 tn = tiles[bn];
+            const CUtensorMap *tmn = maps + 2 * tn.x + (G[tn.x].cur ^ phase);
+            asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                         ::"l"(reinterpret_cast<unsigned long long>(tmn)), "r"(tn.y + OX - S::HX), "r"(tn.z), "r"(0)
+                         : "memory");
+        }
+    }
+    // the grid's parameter block, while the tile copy is in flight
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(Pall + t.x);
+        int4 *dst = reinterpret_cast<int4 *>(&Ps);
+        for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kThreads) dst[k] = src[k];
+    }
+    const bool ok = mbar_wait(bar_a, 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicExch(g.err, 1);
+            mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
+        }
+        return;
+    }
+    flow_phase<float, true>(Ps.cf, tile, su, nullptr, nullptr, tid);
+    __syncthreads();
+    phase2_packed<true, Lim>(Ps, reinterpret_cast<const float2 *>(tile), reinterpret_cast<const float2 *>(su), lane,
+                             ty, t.y, t.z, static_cast<float *>(g.buf[in ^ 1]));
+}
+
+cudaError_t launch_step_tma_batch(const Params *Pall, const BatchGrid *G, const void *maps, const int4 *tiles,
+                                  int ntiles, int limiter, int phase, cudaStream_t st)
+{
+    using S = TmaShape<float>;
+    if (ntiles <= 0) return cudaSuccess;
+    const dim3 block(kTmaTX, S::TT);
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    if (limiter == 0) k_step_tma_batch<0><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
+    else if (limiter == 1) k_step_tma_batch<1><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
+    else k_step_tma_batch<2><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -513,6 +604,9 @@ cudaError_t tma_prepare()
     set((const void *)k_step_tma<float, true, 0, true>, TmaShape<float>::smem_bytes);
     set((const void *)k_step_tma<float, true, 1, true>, TmaShape<float>::smem_bytes);
     set((const void *)k_step_tma<float, true, 2, true>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma_batch<0>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma_batch<1>, TmaShape<float>::smem_bytes);
+    set((const void *)k_step_tma_batch<2>, TmaShape<float>::smem_bytes);
     return e;
 }
 

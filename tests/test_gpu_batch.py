@@ -110,7 +110,7 @@ def test_autotune_keeps_state_and_parity(orc, lbm, prec):
     s.step(10)
     before = s.get_state()
     choice = s.autotune(3)
-    assert choice in (1, 2, 3, 4, 5, 6, 7)
+    assert choice in (1, 2, 3, 4, 5, 6, 7, 8)
     assert s.step_kernel == choice
     assert np.array_equal(s.get_state(), before)
     assert s.step_count == 10
@@ -124,11 +124,11 @@ def test_autotune_keeps_state_and_parity(orc, lbm, prec):
 
 
 def test_batch_runs_large_members_on_their_own_kernels(lbm):
-    """Members whose own kernel is TMA-staged and fills a wave of its tiles (here a float32
-    640 x 512 grid and a float64 1280 x 1024 grid) run that kernel inside the batch's graph:
-    bit-identical to stepping them alone. The small members share the packed tile kernel.
-    Stepping a large member alone an odd number of times between batch steps flips its
-    buffer parity, and the batch recaptures its graph."""
+    """A float64 1280 x 1024 member on the streaming kernel runs that kernel inside the batch's
+    graph, and a float32 640 x 512 member on the tile kernel goes to the batched tile kernel:
+    both bit-identical to stepping them alone.  The Sod member shares the packed plain kernel.
+    Stepping a member alone an odd number of times between batch steps flips its buffer
+    parity, and the batch recaptures its graph."""
     specs = [(wl.shear_layer(640, ny=512, seed=3), 1, 0), (wl.shear_layer(1280, ny=1024, seed=4), 0, 5),
              (wl.sod(200, 4), 0, 0), (wl.shear_layer(96, ny=40, seed=5), 1, 0)]
 
@@ -159,4 +159,67 @@ def test_batch_runs_large_members_on_their_own_kernels(lbm):
             assert np.abs(got - want).max() <= ROUNDOFF[prec] * np.abs(want).max(), p.name
     b.close()
     for s in batched + solo:
+        s.close()
+
+
+def _tma_mix():
+    """Uneven grids for the batched TMA-staged kernels: float32 and float64 (double-float),
+    from one tile to many, ragged edges, walls with the energy-flux correction, every limiter."""
+    out = []
+    for k, (nx, ny) in enumerate([(32, 32), (48, 40), (100, 70), (333, 129), (640, 256)]):
+        out.append((wl.shear_layer(nx, ny=ny, seed=11 + k), 1, (0, 1, 2)[k % 3]))
+        out.append((wl.shock_interface(nx=nx, ny=ny, steps=1), 0, (2, 0, 1)[k % 3]))
+    q = wl.shear_layer(96, ny=66, seed=21)
+    q.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
+    out.append((q, 0, 0))
+    out.append((q, 1, 0))
+    return out
+
+
+def test_batched_tma_kernels_equal_solo_bit_for_bit(lbm):
+    """Members on the tile kernel (float32) and the double-float kernel (float64) step in the
+    batched TMA-staged launches with the arithmetic of their single-grid kernels: bit-identical
+    to stepping alone, over a graph replay, an odd step and a solo step in between."""
+    probs = _tma_mix()
+    batched = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
+    solo = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
+    for s in batched:
+        assert s.step_kernel == (8 if s.precision == 0 else 2)
+    b = lbm.Batch(batched)
+    b.step(9)
+    batched[3].step(1)
+    solo[3].step(1)
+    b.step(2)
+    for s in solo:
+        s.step(11)
+    for (p, prec, lim), x, y in zip(probs, batched, solo):
+        assert np.array_equal(x.get_state(), y.get_state()), (p.name, p.nx, p.ny, prec, lim)
+    b.close()
+
+
+def test_batched_tma_members_against_oracle(orc, lbm):
+    """Each member of a mixed batch after 60 batched steps against the oracle: float64
+    (double-float kernel) to 1e-10 on rho, u, T; float32 (tile kernel) within L1 1e-4 and
+    max 1e-3."""
+    from _gpu_helpers import l1_rel, max_rel
+    probs = _tma_mix()
+    batched = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
+    b = lbm.Batch(batched)
+    b.step(60)
+    b.close()
+    for (p, prec, lim), s in zip(probs, batched):
+        O = orc.Oracle(p.nx, p.ny, p.dx, p.dt, p.gamma, p.s, lim, p.bc)
+        O.init(*p.fields())
+        O.step(60)
+        if prec == 0:
+            errs = fp64_errors(s, O)
+            assert max(errs.values()) <= 1e-10, (p.name, p.nx, p.ny, lim, errs)
+        else:
+            g, r = s.moments(), O.moments()
+            for a, c in ((g[0], r[0]), (g[3], r[3])):
+                assert l1_rel(a, c) <= 1e-4 and max_rel(a, c) <= 1e-3, (p.name, p.nx, p.ny, lim)
+            du = np.hypot(g[1] - r[1], g[2] - r[2])
+            un = np.hypot(r[1], r[2])
+            assert du.sum() / un.sum() <= 1e-4 and du.max() / un.max() <= 1e-3, (p.name, p.nx, p.ny, lim)
         s.close()
