@@ -58,17 +58,17 @@ TOTALS_EVERY = 100
 # of the kernel sources it was captured from.  bench reports the traffic only while the sources
 # still hash to that value, else null.
 TRAFFIC_PER_CELL = {
-    "f32": {"bytes": 125.87, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
-            "sha": "4d6d8aaddb3ad2e2"},
+    "f32": {"bytes": 125.86, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "c198c0464407fa65"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
-            "sha": "1fae702a20fe4afb"},
-    "dd": {"bytes": None, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
-           "sha": None},
+            "sha": "04e90657479a99f4"},
+    "dd": {"bytes": 248.06, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": "ffb34e6c055f2387"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
 # float64 kernel, counted by ncu on the same sources (profiles/k_step_dd_f64_shear_layer.md);
 # None when the sources changed since.
-DD_FP32_OPS = {"ops": None, "sha": None}
+DD_FP32_OPS = {"ops": 3878.3, "sha": "ffb34e6c055f2387"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 
@@ -117,6 +117,7 @@ def parse_args(argv=None):
     ap.add_argument("--serving-steps", type=int, default=1000)
     ap.add_argument("--serving-max-grid", type=int, nargs=2, default=(2048, 512), metavar=("NX", "NY"))
     ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-grid batched-stepping measurement")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the FP32-vs-FP64 runs at each configuration's stated length")
     return ap.parse_args(argv)
@@ -777,9 +778,11 @@ def finish(line, p, args, rank, world):
                 "shock_interface_4096x1024": guarded(precision_study, lbm, wl.shock_interface(), dev, 5000,
                                                      every=100, delta_every=500),
             }
-    if rank == 0 and args.serving_requests > 0:
+    if rank == 0 and not args.no_batch:
         import torch
         line["batch"] = guarded(batch_measure, torch.cuda.current_device())
+    if rank == 0 and args.serving_requests > 0:
+        import torch
         line["serving"] = guarded(serving_measure, args.serving_requests, args.serving_steps,
                                   args.serving_max_grid[0], args.serving_max_grid[1], torch.cuda.current_device())
     if rank == 0 and not args.no_cpu_baseline:
