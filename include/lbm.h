@@ -211,13 +211,13 @@ int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
    steps are launch-bound.  The contexts must be initialised, share one device and one
    stream, and stay alive while the batch exists.  Each step of lbm_batch_step runs, per
    group of contexts with the same precision and limiter, one batched ghost-fill launch and
-   up to two fused-step launches over tile lists spanning the group's grids:
+   fused-step launches over the tiles of the group's grids:
    - contexts whose step kernel is the TMA-staged tile kernel (float32) or the double-float
      kernel (float64), i.e. the automatic choice on grids of at least 32 x 32 (float64) or
-     32 x 16 (float32), have their tiles in one launch of that kernel's batched form (one
-     CTA per tile; each tile names its grid, whose parameters the CTA stages in shared
-     memory and whose tensor map it reads from the batch's table), with the arithmetic of
-     the single-grid kernel, bit for bit;
+     32 x 16 (float32), have their tiles in one launch of that kernel's batched form per 128
+     such grids (one CTA per tile; the launch's parameters hold each grid's tensor map,
+     output buffer and tile count, and the CTA stages its grid's coefficients in shared
+     memory), with the arithmetic of the single-grid kernel, bit for bit;
    - the other grids share the packed plain kernel, whose persistent CTAs walk a tile list
      (float32: 256-cell tiles, float64: 64-cell tiles, which spread small float64 grids over
      more SMs; 32 columns wide, or TX = the smallest power of two >= nx for narrower grids)
@@ -227,8 +227,7 @@ int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
      takes part in its group's ghost launch only and steps with its own kernel, launched on
      one of eight forked streams so that such grids overlap, bit for bit.
    Pairs of steps are replayed from a CUDA graph captured on the first call with n >= 2
-   (recaptured when a context on its own kernel was stepped alone an odd number of times
-   since).  Tiles are independent, so a grid's result does not depend on the other members
+   (recaptured when a context was stepped alone an odd number of times since).  Tiles are independent, so a grid's result does not depend on the other members
    of its batch (bit for bit).
    Contexts may also be stepped alone between batch steps.  Errors: LBM_ERR_ARG (NULL, empty, mixed device or stream, a
    context listed twice), LBM_ERR_STATE (uninitialised context, n <= 0), LBM_ERR_OOM,

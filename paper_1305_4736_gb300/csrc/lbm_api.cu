@@ -1014,13 +1014,12 @@ struct lbm_batch {
         int4 *dT = nullptr;
         int ntiles = 0, max_ghost = 0;
         int nt = lbm::kBatchThreads;             // threads (= cells) per tile
-        // batched TMA-staged kernel: CUtensorMap[2n] | Coef<dd>[n] (float64) | int4[ntt]
+        // batched TMA-staged kernel: the members it serves (indices into members, in launch
+        // order) and their TileGrid blocks (Coef<float> or Coef<dd> by precision)
+        std::vector<int> tk;
         void *tblock = nullptr;
         size_t tbytes = 0;
-        CUtensorMap *dM = nullptr;
-        lbm::Coef<lbm::dd> *dC = nullptr;
-        int4 *dTT = nullptr;
-        int ntt = 0;
+        int ntt = 0;                             // tiles per step
     };
     std::vector<lbm_ctx *> ctxs;
     std::vector<Group> groups;
@@ -1029,7 +1028,8 @@ struct lbm_batch {
     // that kernel, launched on kForks forked streams so that the grids' kernels overlap; their
     // buffer parity at capture time
     static constexpr int kForks = 8;
-    std::vector<int> solo, solo_cur;
+    std::vector<int> solo;
+    std::vector<int> cap_cur;                   // every context's buffer parity at graph capture
     cudaStream_t fork[kForks] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kForks] = {};
     cudaStream_t stream = nullptr, cap = nullptr;
@@ -1051,6 +1051,38 @@ cudaError_t batch_upload_cur(lbm_batch *b)
     return cudaSuccess;
 }
 
+// The group's batched TMA-staged launches (kTmaBatchGrids grids each), with every member's
+// input map, output buffer and flag resolved for this step's parity.
+cudaError_t batch_launch_tma(lbm_batch *b, const lbm_batch::Group &g, int phase, cudaStream_t st)
+{
+    static thread_local lbm::TmaBatchArgs A;
+    const bool f64 = g.prec == LBM_FP64;
+    const int tr = f64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR;
+    const size_t tgb = f64 ? sizeof(lbm::TileGrid<lbm::Coef<lbm::dd>>) : sizeof(lbm::TileGrid<lbm::Coef<float>>);
+    for (size_t c0 = 0; c0 < g.tk.size(); c0 += lbm::kTmaBatchGrids) {
+        const int n = (int)std::min<size_t>(lbm::kTmaBatchGrids, g.tk.size() - c0);
+        int tiles = 0;
+        for (int k = 0; k < n; k++) {
+            const lbm_ctx *c = b->ctxs[g.members[g.tk[c0 + k]]];
+            const int in = c->cur ^ phase;
+            A.map[k] = c->tmap[in];
+            A.out[k] = c->f[in ^ 1];
+            A.err[k] = c->tma_err;
+            A.first[k] = tiles;
+            A.ntx[k] = (c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX;
+            tiles += A.ntx[k] * ((c->P.ny + tr - 1) / tr);
+        }
+        A.first[n] = tiles;
+        A.n = n;
+        const char *tg = (const char *)g.tblock + c0 * tgb;
+        const cudaError_t ce =
+            f64 ? lbm::launch_step_dd_batch(A, (const lbm::TileGrid<lbm::Coef<lbm::dd>> *)tg, g.limiter, st)
+                : lbm::launch_step_tma_batch(A, (const lbm::TileGrid<lbm::Coef<float>> *)tg, g.limiter, st);
+        if (ce != cudaSuccess) return ce;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
 {
     cudaError_t ce = cudaSuccess;
@@ -1067,10 +1099,7 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
     for (auto &g : b->groups) {
         ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
                                     g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
-        if (ce == cudaSuccess && g.ntt > 0)
-            ce = g.prec == LBM_FP64
-                     ? lbm::launch_step_dd_batch(g.dP, g.dC, g.dG, g.dM, g.dTT, g.ntt, g.limiter, phase, st)
-                     : lbm::launch_step_tma_batch(g.dP, g.dG, g.dM, g.dTT, g.ntt, g.limiter, phase, st);
+        if (ce == cudaSuccess && !g.tk.empty()) ce = batch_launch_tma(b, g, phase, st);
         if (ce != cudaSuccess) return ce;
     }
     for (size_t j = 0; j < b->solo.size(); j++) {
@@ -1154,10 +1183,10 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
                 if (!g.own[k] && !g.tma[k]) cells += (long long)b->ctxs[g.members[k]]->P.nx * b->ctxs[g.members[k]]->P.ny;
             g.nt = cells >= 4LL * lbm::kBatchThreads * sms ? lbm::kBatchThreads : lbm::kBatchThreadsFp64;
         }
-        std::vector<int4> tiles, ttiles;
+        std::vector<int4> tiles;
         std::vector<lbm::Params> hp;
-        std::vector<CUtensorMap> hm;
-        std::vector<lbm::Coef<lbm::dd>> hc;
+        std::vector<lbm::TileGrid<lbm::Coef<float>>> htf;
+        std::vector<lbm::TileGrid<lbm::Coef<lbm::dd>>> htd;
         const int tr = g.prec == LBM_FP64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR;
         for (size_t k = 0; k < g.members.size(); k++) {
             const lbm_ctx *c = b->ctxs[g.members[k]];
@@ -1165,13 +1194,15 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             hp.back().wrap = 0;                      // the batched ghost fill writes every ghost cell
             g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->tma_err, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
-            CUtensorMap none{};
-            hm.push_back(g.tma[k] ? c->tmap[0] : none);
-            hm.push_back(g.tma[k] ? c->tmap[1] : none);
-            if (g.prec == LBM_FP64) hc.push_back(c->cdd);
             if (g.tma[k]) {
-                for (int y = 0; y < c->P.ny; y += tr)
-                    for (int x = 0; x < c->P.nx; x += lbm::kTmaTX) ttiles.push_back(make_int4((int)k, x, y, 0));
+                g.tk.push_back((int)k);
+                g.ntt += ((c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX) * ((c->P.ny + tr - 1) / tr);
+                if (g.prec == LBM_FP64)
+                    htd.push_back(lbm::TileGrid<lbm::Coef<lbm::dd>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
+                                                                    c->P.plane, 0, c->cdd});
+                else
+                    htf.push_back(lbm::TileGrid<lbm::Coef<float>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
+                                                                  c->P.plane, 0, c->P.cf});
                 continue;
             }
             if (g.own[k]) continue;                  // ghost cells only
@@ -1197,22 +1228,12 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             ce = cudaMemcpyAsync(g.dG, g.hG.data(), g.hG.size() * sizeof(lbm::BatchGrid), cudaMemcpyHostToDevice,
                                  b->stream);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(g.dT, tiles.data(), nt, cudaMemcpyHostToDevice, b->stream);
-        g.ntt = (int)ttiles.size();
-        if (ce == cudaSuccess && g.ntt > 0) {
-            const size_t nm = up(hm.size() * sizeof(CUtensorMap)), nc = up(hc.size() * sizeof(lbm::Coef<lbm::dd>));
-            g.tbytes = nm + nc + ttiles.size() * sizeof(int4);
+        if (ce == cudaSuccess && !g.tk.empty()) {
+            const void *src = htd.empty() ? (const void *)htf.data() : (const void *)htd.data();
+            g.tbytes = htd.empty() ? htf.size() * sizeof(htf[0]) : htd.size() * sizeof(htd[0]);
             g.tblock = b->alloc.alloc(g.tbytes, b->stream, b->alloc.user);
             if (!g.tblock) { cudaGetLastError(); lbm_batch_destroy(b); return fail(nullptr, LBM_ERR_OOM, "batch tables"); }
-            g.dM = (CUtensorMap *)g.tblock;
-            g.dC = (lbm::Coef<lbm::dd> *)((char *)g.tblock + nm);
-            g.dTT = (int4 *)((char *)g.tblock + nm + nc);
-            ce = cudaMemcpyAsync(g.dM, hm.data(), hm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, b->stream);
-            if (ce == cudaSuccess && !hc.empty())
-                ce = cudaMemcpyAsync(g.dC, hc.data(), hc.size() * sizeof(lbm::Coef<lbm::dd>), cudaMemcpyHostToDevice,
-                                     b->stream);
-            if (ce == cudaSuccess)
-                ce = cudaMemcpyAsync(g.dTT, ttiles.data(), ttiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                                     b->stream);
+            ce = cudaMemcpyAsync(g.tblock, src, g.tbytes, cudaMemcpyHostToDevice, b->stream);
         }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
         if (ce != cudaSuccess) { lbm_batch_destroy(b); return cuda_fail(nullptr, ce, "batch tables"); }
@@ -1239,10 +1260,10 @@ int lbm_batch_step(lbm_batch *b, int n)
     if (ce == cudaSuccess) ce = batch_upload_cur(b);
     if (ce != cudaSuccess) return cuda_fail(c0, ce, "batch");
     if (b->exec2) {
-        // the graph's own-kernel launches name their buffers: recapture if a context was
-        // stepped alone an odd number of times since the capture
+        // the graph's own-kernel and batched TMA-staged launches name their buffers: recapture
+        // if a context was stepped alone an odd number of times since the capture
         bool same = true;
-        for (size_t k = 0; k < b->solo.size(); k++) same = same && b->ctxs[b->solo[k]]->cur == b->solo_cur[k];
+        for (size_t k = 0; k < b->ctxs.size(); k++) same = same && b->ctxs[k]->cur == b->cap_cur[k];
         if (!same) {
             ce = cudaStreamSynchronize(b->stream);
             if (ce == cudaSuccess) ce = cudaGraphExecDestroy(b->exec2);
@@ -1251,8 +1272,8 @@ int lbm_batch_step(lbm_batch *b, int n)
         }
     }
     if (n >= 2 && !b->exec2) {
-        b->solo_cur.clear();
-        for (int i : b->solo) b->solo_cur.push_back(b->ctxs[i]->cur);
+        b->cap_cur.clear();
+        for (lbm_ctx *c : b->ctxs) b->cap_cur.push_back(c->cur);
         // capture two steps (both buffer parities) once; replays read the tables' current contents
         cudaGraph_t graph = nullptr;
         ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);

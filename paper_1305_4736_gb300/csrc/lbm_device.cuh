@@ -517,8 +517,8 @@ __device__ __forceinline__ void unbutterfly2_diag(float2 S, float2 X, float2 Y, 
 
 // acc[pr] = collision term of pair pr (dt M^-1 S (f_hat - f_hat^eq), Eq. 3 with the
 // energy-flux correction of Sec. II).
-template <bool Dev>
-__device__ __forceinline__ void collide2(const Params &P, const Shells2 &sh, float drho, float jx, float jy,
+template <bool Dev, typename PP>
+__device__ __forceinline__ void collide2(const PP &P, const Shells2 &sh, float drho, float jx, float jy,
                                          float de, float ir, float dxux, float dyux, float dxuy, float dyuy,
                                          float2 *acc)
 {

@@ -1,6 +1,7 @@
 // lbm_internal.h -- launchers shared between the host API and the kernel units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_dd.cuh"
@@ -79,14 +80,33 @@ struct TmaShape {
     static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * (sizeof(R) == sizeof(float) ? 2 : 3) * UW * UH;
 };
 bool tma_supported(const Params &P, int prec);
-// Batched TMA-staged steps: one CTA per tile of a list {grid, x0, y0, 0} spanning the grids of a
-// batch group (tiles of TmaShape<R>); `maps` holds two tensor maps per grid (buffer 0, buffer
-// 1), `phase` as launch_step_batch.  float32 (the tile kernel) and float64 in double-float
-// arithmetic (`coefs`: one Coef<dd> per grid).
-cudaError_t launch_step_tma_batch(const Params *Pall, const BatchGrid *G, const void *maps, const int4 *tiles,
-                                  int ntiles, int limiter, int phase, cudaStream_t st);
-cudaError_t launch_step_dd_batch(const Params *Pall, const void *coefs, const BatchGrid *G, const void *maps,
-                                 const int4 *tiles, int ntiles, int limiter, int phase, cudaStream_t st);
+// Batched TMA-staged steps over the tiles of up to kTmaBatchGrids grids of a batch group, one
+// CTA per tile of kTmaTX x TmaShape<R>::TR cells: grid k owns the launch's tiles first[k] ..
+// first[k+1] - 1, row by row, ntx[k] to a row.  A CTA finds its grid and tile from blockIdx
+// and this parameter block alone, so that its tile copy is issued before any load from global
+// memory; the host resolves each grid's input map, output buffer and error flag for the
+// launch's buffer parity.  float32 (the tile kernel) and float64 in double-float arithmetic.
+constexpr int kTmaBatchGrids = 128;
+struct TmaBatchArgs {
+    CUtensorMap map[kTmaBatchGrids];   // grid k's input buffer (box of TmaShape<R>)
+    void *out[kTmaBatchGrids];          // grid k's output buffer
+    int *err[kTmaBatchGrids];           // grid k's copy-wait flag
+    int first[kTmaBatchGrids + 1];      // first[n] = tiles of the launch
+    int ntx[kTmaBatchGrids];            // tiles per row of grid k
+    int n;                              // grids of the launch
+};
+// Per-grid block of a batched launch (global memory, one per grid in launch order): the
+// geometry and the coefficients that the tile kernels read (C = Coef<float> or Coef<dd>); each
+// CTA copies its grid's block to shared memory while its tile copy is in flight.
+template <typename C>
+struct TileGrid {
+    int nx, ny, pitch, has_c9;
+    long long plane, pad;
+    C cf;
+};
+cudaError_t launch_step_tma_batch(const TmaBatchArgs &A, const TileGrid<Coef<float>> *tg, int limiter,
+                                  cudaStream_t st);
+cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, cudaStream_t st);
 // Failure-path check of the bounded mbarrier waits (lbm_wait_selftest): *flag = 1 when the
 // wait on a phase that nothing completes gave up at its limit; *ms = the kernel's duration.
 cudaError_t wait_selftest(int *flag, float *ms);

@@ -142,8 +142,9 @@ __device__ __forceinline__ dd slope_dd(dd a, dd b)
 // The tile body shared by the single-grid and the batched kernel: the staged float64 tile in
 // shared memory (smraw) is split, then phases 1 and 2 produce the tile's new float64 values.
 // ---------------------------------------------------------------------------
-template <int Lim, bool C9>
-__device__ __forceinline__ void dd_tile(const Params &P, const Coef<dd> &C, unsigned char *smraw,
+// P: the context's Params, or the TileGrid block of a batched launch (nx, ny, pitch, plane).
+template <int Lim, bool C9, typename PP>
+__device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned char *smraw,
                                         double *__restrict__ fout, int x0, int y0)
 {
     using S = TmaShape<double>;
@@ -349,62 +350,47 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
 }
 
 // ---------------------------------------------------------------------------
-// Batched form: one CTA per tile of a list spanning the grids of a batch group.  A tile
-// {grid, x0, y0} names its grid: the CTA copies that grid's parameter block and double-float
-// coefficients into shared memory and issues its tile copy with the grid's tensor map from
-// global memory.  The ghost cells come from the batched ghost fill, so no x wrap.  The
-// energy-flux correction runs for every grid; its factors are zero where s8 = s5, which leaves
-// the residuals unchanged bit for bit.
+// Batched form: one CTA per tile of the launch's grids (TmaBatchArgs).  Thread 0 issues the
+// tile copy with the grid's tensor map from the parameter block, then the CTA copies the grid's
+// TileGrid block (geometry and double-float coefficients) into shared memory while the copy is
+// in flight.  The ghost cells come from the batched ghost fill, so no x wrap.  The energy-flux
+// correction runs for every grid; its factors are zero where s8 = s5, which leaves the
+// residuals unchanged bit for bit.
 // ---------------------------------------------------------------------------
 template <int Lim>
 __global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
-k_step_dd_batch(const Params *__restrict__ Pall, const Coef<dd> *__restrict__ Call, const BatchGrid *__restrict__ G,
-                const CUtensorMap *__restrict__ maps, const int4 *__restrict__ tiles, int phase)
+k_step_dd_batch(const __grid_constant__ TmaBatchArgs A, const TileGrid<Coef<dd>> *__restrict__ TG)
 {
     using S = TmaShape<double>;
+    using T = TileGrid<Coef<dd>>;
+    static_assert(sizeof(T) % 16 == 0, "TileGrid copy");
     extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(16) Params Ps;
-    __shared__ __align__(16) Coef<dd> Cs;
+    __shared__ __align__(16) T Ts;
     __shared__ __align__(8) unsigned long long bar;
     const int tid = threadIdx.y * kTmaTX + threadIdx.x;
     constexpr int kThreads = kTmaTX * S::TT;
-    const int4 t = tiles[blockIdx.x];
-    const BatchGrid g = G[t.x];
-    const int in = g.cur ^ phase;
+    int x0, y0;
+    const int g = batch_tile(A, blockIdx.x, S::TR, x0, y0);
     const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const CUtensorMap *tm = maps + 2 * t.x + in;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(smraw);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
-                     "r"((unsigned)S::tile_bytes) : "memory");
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(t.y + OX - S::HX), "r"(t.z),
-                     "r"(0), "r"(bar_a) : "memory");
-    }
-    // the grid's parameter block and coefficients, while the tile copy is in flight
+    if (tid == 0)
+        batch_issue<S::TR, S::HX>(A, g, x0, y0, (unsigned)__cvta_generic_to_shared(smraw), bar_a,
+                                  (unsigned)S::tile_bytes, 0);
+    // the grid's block, while the tile copy is in flight
     {
-        const int4 *src = reinterpret_cast<const int4 *>(Pall + t.x);
-        int4 *dst = reinterpret_cast<int4 *>(&Ps);
-        for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kThreads) dst[k] = src[k];
-        const int4 *srcc = reinterpret_cast<const int4 *>(Call + t.x);
-        int4 *dstc = reinterpret_cast<int4 *>(&Cs);
-        for (int k = tid; k < (int)(sizeof(Coef<dd>) / sizeof(int4)); k += kThreads) dstc[k] = srcc[k];
+        const int4 *src = reinterpret_cast<const int4 *>(TG + g);
+        int4 *dst = reinterpret_cast<int4 *>(&Ts);
+        for (int k = tid; k < (int)(sizeof(T) / sizeof(int4)); k += kThreads) dst[k] = src[k];
     }
+    __syncthreads();                            // the barrier is initialised
     const bool ok = mbar_wait(bar_a, 0);
     if (!__syncthreads_and(ok)) {
         if (tid == 0) {
-            atomicExch(g.err, 1);
+            atomicExch(A.err[g], 1);
             mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
         }
         return;
     }
-    dd_tile<Lim, true>(Ps, Cs, smraw, static_cast<double *>(g.buf[in ^ 1]), t.y, t.z);
+    dd_tile<Lim, true>(Ts, Ts.cf, smraw, static_cast<double *>(A.out[g]), x0, y0);
 }
 
 // Coefficients in double-float from the float64 tables (host).
@@ -448,17 +434,15 @@ cudaError_t launch_step_dd(const Params &P, const void *coef, const void *tmap, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_dd_batch(const Params *Pall, const void *coefs, const BatchGrid *G, const void *maps,
-                                 const int4 *tiles, int ntiles, int limiter, int phase, cudaStream_t st)
+cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, cudaStream_t st)
 {
     using S = TmaShape<double>;
+    const int ntiles = A.first[A.n];
     if (ntiles <= 0) return cudaSuccess;
     const dim3 block(kTmaTX, S::TT);
-    const Coef<dd> *C = static_cast<const Coef<dd> *>(coefs);
-    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
-    if (limiter == 0) k_step_dd_batch<0><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
-    else if (limiter == 1) k_step_dd_batch<1><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
-    else k_step_dd_batch<2><<<ntiles, block, S::smem_bytes, st>>>(Pall, C, G, m, tiles, phase);
+    if (limiter == 0) k_step_dd_batch<0><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else if (limiter == 1) k_step_dd_batch<1><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else k_step_dd_batch<2><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
     return cudaGetLastError();
 }
 

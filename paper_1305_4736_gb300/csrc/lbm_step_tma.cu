@@ -23,11 +23,12 @@ namespace lbm {
 
 // Phase 2 of the float32 kernel on population pairs: the staged tile is 8 planes of
 // pairs (pair_q(pr), pair_q(pr) + 4), read and written one pair per access.
-template <bool Dev, int Lim, typename S = TmaShape<float>>
-__device__ __forceinline__ void phase2_packed(const Params &P, const float2 *tile, const float2 *suv,
+// P: the context's Params, or the TileGrid block of a batched launch (the fields read here).
+template <bool Dev, int Lim, typename S = TmaShape<float>, typename PP = Params>
+__device__ __forceinline__ void phase2_packed(const PP &P, const float2 *tile, const float2 *suv,
                                               int lane, int ty, int x0, int y0, float *__restrict__ fout)
 {
-    const Coef<float> &C = coef<float>(P);
+    const Coef<float> &C = P.cf;
     const int gx = x0 + lane;
     const int r0 = ty * S::KR;
     const float2 *col = tile + (lane + S::HX);
@@ -307,85 +308,64 @@ k_step_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap
 }
 
 // ---------------------------------------------------------------------------
-// Batched form (float32): one CTA per tile of a list spanning the grids of a batch group.  A
-// tile {grid, x0, y0} names its grid: the CTA copies that grid's parameter block into shared
-// memory and issues its tile copy with the grid's tensor map from global memory; the
+// Batched form (float32): one CTA per tile of the launch's grids (TmaBatchArgs).  Thread 0
+// issues the tile copy with the grid's tensor map from the parameter block, then the CTA
+// copies the grid's TileGrid block into shared memory while the copy is in flight; the
 // arithmetic is that of k_step_tma.  The ghost cells come from the batched ghost fill, so no
-// x wrap.  The L2 prefetch goes to the tile half a resident wave further down the list.
+// x wrap.
 // ---------------------------------------------------------------------------
 template <int Lim>
 __global__ void __launch_bounds__(kTmaTX * TmaShape<float>::TT, TmaShape<float>::CTAS)
-k_step_tma_batch(const Params *__restrict__ Pall, const BatchGrid *__restrict__ G, const CUtensorMap *__restrict__ maps,
-                 const int4 *__restrict__ tiles, int ntiles, int phase)
+k_step_tma_batch(const __grid_constant__ TmaBatchArgs A, const TileGrid<Coef<float>> *__restrict__ TG)
 {
     using S = TmaShape<float>;
+    using T = TileGrid<Coef<float>>;
+    static_assert(sizeof(T) % 16 == 0, "TileGrid copy");
     extern __shared__ __align__(128) unsigned char smraw[];
     float *tile = reinterpret_cast<float *>(smraw);
     float *su = tile + NQ * S::PL;
-    __shared__ __align__(16) Params Ps;
+    __shared__ __align__(16) T Ts;
     __shared__ __align__(8) unsigned long long bar;
 
     const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * kTmaTX + lane;
     constexpr int kThreads = kTmaTX * S::TT;
-    const int4 t = tiles[blockIdx.x];
-    const BatchGrid g = G[t.x];
-    const int in = g.cur ^ phase;
+    int x0, y0;
+    const int g = batch_tile(A, blockIdx.x, S::TR, x0, y0);
     const unsigned bar_a = (unsigned)__cvta_generic_to_shared(&bar);
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const CUtensorMap *tm = maps + 2 * t.x + in;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(tile);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
-                     "r"((unsigned)S::tile_bytes) : "memory");
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(tm)), "r"(t.y + OX - S::HX), "r"(t.z),
-                     "r"(0), "r"(bar_a) : "memory");
-        unsigned nsm;
-        asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
-        const long long bn = (long long)blockIdx.x + (long long)S::CTAS * nsm / 2;
-        if (bn < ntiles) {
-            const int4 tn = tiles[bn];
-            const CUtensorMap *tmn = maps + 2 * tn.x + (G[tn.x].cur ^ phase);
-            asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
-                         ::"l"(reinterpret_cast<unsigned long long>(tmn)), "r"(tn.y + OX - S::HX), "r"(tn.z), "r"(0)
-                         : "memory");
-        }
-    }
-    // the grid's parameter block, while the tile copy is in flight
+    if (tid == 0)
+        batch_issue<S::TR, S::HX>(A, g, x0, y0, (unsigned)__cvta_generic_to_shared(tile), bar_a,
+                                  (unsigned)S::tile_bytes, S::CTAS);
+    // the grid's block, while the tile copy is in flight
     {
-        const int4 *src = reinterpret_cast<const int4 *>(Pall + t.x);
-        int4 *dst = reinterpret_cast<int4 *>(&Ps);
-        for (int k = tid; k < (int)(sizeof(Params) / sizeof(int4)); k += kThreads) dst[k] = src[k];
+        const int4 *src = reinterpret_cast<const int4 *>(TG + g);
+        int4 *dst = reinterpret_cast<int4 *>(&Ts);
+        for (int k = tid; k < (int)(sizeof(T) / sizeof(int4)); k += kThreads) dst[k] = src[k];
     }
+    __syncthreads();                            // the barrier is initialised
     const bool ok = mbar_wait(bar_a, 0);
     if (!__syncthreads_and(ok)) {
         if (tid == 0) {
-            atomicExch(g.err, 1);
+            atomicExch(A.err[g], 1);
             mbar_wait(bar_a, 0);               // let a late copy land before the CTA exits (bounded)
         }
         return;
     }
-    flow_phase<float, true>(Ps.cf, tile, su, nullptr, nullptr, tid);
+    flow_phase<float, true>(Ts.cf, tile, su, nullptr, nullptr, tid);
     __syncthreads();
-    phase2_packed<true, Lim>(Ps, reinterpret_cast<const float2 *>(tile), reinterpret_cast<const float2 *>(su), lane,
-                             ty, t.y, t.z, static_cast<float *>(g.buf[in ^ 1]));
+    phase2_packed<true, Lim>(Ts, reinterpret_cast<const float2 *>(tile), reinterpret_cast<const float2 *>(su), lane,
+                             ty, x0, y0, static_cast<float *>(A.out[g]));
 }
 
-cudaError_t launch_step_tma_batch(const Params *Pall, const BatchGrid *G, const void *maps, const int4 *tiles,
-                                  int ntiles, int limiter, int phase, cudaStream_t st)
+cudaError_t launch_step_tma_batch(const TmaBatchArgs &A, const TileGrid<Coef<float>> *tg, int limiter,
+                                  cudaStream_t st)
 {
     using S = TmaShape<float>;
+    const int ntiles = A.first[A.n];
     if (ntiles <= 0) return cudaSuccess;
     const dim3 block(kTmaTX, S::TT);
-    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
-    if (limiter == 0) k_step_tma_batch<0><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
-    else if (limiter == 1) k_step_tma_batch<1><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
-    else k_step_tma_batch<2><<<ntiles, block, S::smem_bytes, st>>>(Pall, G, m, tiles, ntiles, phase);
+    if (limiter == 0) k_step_tma_batch<0><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else if (limiter == 1) k_step_tma_batch<1><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else k_step_tma_batch<2><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
     return cudaGetLastError();
 }
 

@@ -101,6 +101,51 @@ __device__ __noinline__ void wrap_halo(const Params &P, const R *__restrict__ fi
 // move in the same direction: their stencils have the same offsets and only the per-shell
 // constants differ, so their convection runs as one float2 per pair.
 
+// Batched launches: the grid of tile b (the largest k with first[k] <= b, a binary search on
+// the parameter block, uniform across the CTA) and the tile's origin.
+__device__ __forceinline__ int batch_tile(const TmaBatchArgs &A, int b, int tr, int &x0, int &y0)
+{
+    int lo = 0, hi = A.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int local = b - A.first[lo], nt = A.ntx[lo];
+    const int ty = local / nt;
+    x0 = (local - ty * nt) * kTmaTX;
+    y0 = ty * tr;
+    return lo;
+}
+
+// Prologue of a batched tile CTA (thread 0): initialise the tile barrier, issue the copy of
+// grid g's tile at (x0, y0) (tiles of TR rows; the x origin HX columns left of the tile's first
+// interior column), and with ctas > 0 (resident CTAs per SM) prefetch into L2 the tile half a
+// resident wave further down the launch.
+template <int TR, int HX>
+__device__ __forceinline__ void batch_issue(const TmaBatchArgs &A, int g, int x0, int y0, unsigned dst,
+                                            unsigned bar_a, unsigned bytes, int ctas)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(&A.map[g])), "r"(x0 + OX - HX), "r"(y0),
+                 "r"(0), "r"(bar_a) : "memory");
+    if (ctas <= 0) return;
+    unsigned nsm;
+    asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+    const long long bn = (long long)blockIdx.x + (long long)ctas * nsm / 2;
+    if (bn < A.first[A.n]) {
+        int xn, yn;
+        const int gn = batch_tile(A, (int)bn, TR, xn, yn);
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                     ::"l"(reinterpret_cast<unsigned long long>(&A.map[gn])), "r"(xn + OX - HX), "r"(yn), "r"(0)
+                     : "memory");
+    }
+}
+
 template <int Lim>
 __device__ __forceinline__ float2 slope2x2(float2 a, float2 b)
 {
