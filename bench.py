@@ -58,17 +58,17 @@ TOTALS_EVERY = 100
 # of the kernel sources it was captured from.  bench reports the traffic only while the sources
 # still hash to that value, else null.
 TRAFFIC_PER_CELL = {
-    "f32": {"bytes": 125.86, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
-            "sha": "c198c0464407fa65"},
+    "f32": {"bytes": 125.88, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "3611ad9250829546"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "04e90657479a99f4"},
-    "dd": {"bytes": 248.06, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
-           "sha": "ffb34e6c055f2387"},
+    "dd": {"bytes": 247.82, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": "db779b9faf108e12"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
 # float64 kernel, counted by ncu on the same sources (profiles/k_step_dd_f64_shear_layer.md);
 # None when the sources changed since.
-DD_FP32_OPS = {"ops": 3878.3, "sha": "ffb34e6c055f2387"}
+DD_FP32_OPS = {"ops": 3830.3, "sha": "db779b9faf108e12"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 

@@ -13,10 +13,11 @@
 // |lo| <= ulp(hi) / 2.  The pair still holds the value to the same accuracy (lo stays within a
 // few units of 2^-24 of the operands' magnitudes), and every operation here reads both parts,
 // so only the places that look at hi alone renormalise first: the MC slope's comparisons and
-// sign test, the reciprocal's Newton step, and the rounding to float64.  The populations stay
-// float64 in HBM: a staged value is split into hi + lo (rounded to nearest, with integer
-// operations) and an updated value is rounded back to float64 (integer operations as well;
-// float32 <-> float64 conversions run at the float64 rate on this part).
+// sign test, and the reciprocal's Newton step.  The populations stay float64 in HBM: a staged
+// value is split into hi + lo (rounded to nearest) with integer operations, since
+// float32 <-> float64 conversions run at the float64 rate on this part and the split is a phase
+// of its own; an updated value is rounded back to float64 by the float64 pipe, which does that
+// work beside the float32 arithmetic of the other warps.
 //
 // Every float32 operation here uses the _rn intrinsics, which the compiler neither contracts
 // into FMAs nor reorders, so the transformations stay error-free.
@@ -143,7 +144,7 @@ __device__ __forceinline__ dd mc2(dd a, dd b)
 }
 
 // ---------------------------------------------------------------------------
-// float64 <-> double-float with integer operations.
+// float64 -> double-float with integer operations, and back on the float64 pipe.
 // ---------------------------------------------------------------------------
 // x = hi + lo with hi = x rounded to 24 significand bits (half away from zero) and lo the rest
 // rounded to float32 (|lo| <= 2^-25 |x|; the pair carries 48 of x's 53 bits, rounded to
@@ -172,37 +173,13 @@ __device__ __forceinline__ dd dd_split(double x)
               (tiny || big) ? 0.0f : __uint_as_float(__float_as_uint(lo) ^ sign)};
 }
 
-// hi + lo rounded to float64, after renormalising the pair.  The sum is exact in float64
-// whenever lo's exponent is within 29 of hi's (the usual case); below that the part of lo
-// beneath hi's float64 ulp is rounded half up.  hi == 0 returns lo; zero and subnormal float32
-// parts count as 0.
+// hi + lo rounded to float64 (to nearest, ties to even): both parts convert to float64 exactly
+// and one float64 addition rounds their sum.  These three operations run on the float64 pipe,
+// which the step kernel leaves otherwise idle, alongside the float32 and integer work of the
+// other warps; non-finite parts give +-inf or NaN.
 __device__ __forceinline__ double dd_to_double(dd v)
 {
-    v = fast2sum(v.hi, v.lo);
-    const unsigned hb0 = __float_as_uint(v.hi), lb = __float_as_uint(v.lo);
-    const unsigned eh0 = (hb0 >> 23) & 0xFFu, el0 = (lb >> 23) & 0xFFu;
-    // hi zero (or subnormal): the value is lo
-    const bool hz = eh0 == 0u;
-    const unsigned hb = hz ? lb : hb0, eh = hz ? el0 : eh0, el = hz ? 0u : el0;
-    // significands with the implicit bit, in units of hi's float64 ulp: hi -> 24 bits << 29
-    const unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-    const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
-    const int sh = 29 - ((int)eh - (int)el);            // <= 5 for a normalised pair
-    const int rs = min(max(-sh, 1), 63);                 // right shift when sh < 0
-    const unsigned long long cl = ml << max(sh, 0);
-    const unsigned long long cr = rs < 40 ? (ml + (1ull << (rs - 1))) >> rs : 0ull;   // rounded half up
-    const unsigned long long c = el == 0u ? 0ull : (sh >= 0 ? cl : cr);
-    const bool opp = ((hb ^ lb) & 0x80000000u) != 0u && el != 0u;
-    unsigned long long S = opp ? M - c : M + c;
-    int e = (int)eh;
-    const bool down = opp && S < (1ull << 52);           // hi was a power of two
-    const bool upn = !opp && S >= (1ull << 53);          // not reached by a normalised pair
-    S = down ? S << 1 : (upn ? (S + 1ull) >> 1 : S);
-    e += down ? -1 : (upn ? 1 : 0);
-    const unsigned long long sgn = (unsigned long long)(hb & 0x80000000u) << 32;
-    const unsigned long long bits = sgn | ((unsigned long long)(e + 896) << 52) | (S & ((1ull << 52) - 1ull));
-    const unsigned long long out = eh == 0u ? sgn : (eh == 0xFFu ? (sgn | 0x7FF8000000000000ull) : bits);
-    return __longlong_as_double((long long)out);
+    return __dadd_rn((double)v.hi, (double)v.lo);
 }
 
 }  // namespace lbm
