@@ -128,10 +128,18 @@ __device__ __forceinline__ dd shfl_up_dd(dd v)
     return dd{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
 }
 
+// Face differences enter the MC slope normalised (norm_lim, once per difference: each feeds two
+// slopes); the other limiters use them as they are.
+template <int Lim>
+__device__ __forceinline__ dd norm_lim(dd a)
+{
+    return Lim == 0 ? norm(a) : a;
+}
+
 template <int Lim>
 __device__ __forceinline__ dd slope_dd(dd a, dd b)
 {
-    if (Lim == 0) return mc2(a, b);
+    if (Lim == 0) return mc2n(a, b);
     if (Lim == 1) return scale2(b, 2.0f);
     return dd{0.0f, 0.0f};
 }
@@ -190,13 +198,13 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
         const dd *pc = tile + q * S::PL + (lane + S::HX);
         if (sy > 0) {
             const dd w0 = pc[r0 * S::SW], w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW];
-            const dd d0 = w1 - w0, d1 = w2 - w1;
+            const dd d0 = norm_lim<Lim>(w1 - w0), d1 = norm_lim<Lim>(w2 - w1);
             yw[q] = w2;
             yd[q] = d1;
             ym[q] = slope_dd<Lim>(d0, d1);
         } else {
             const dd w1 = pc[(r0 + 1) * S::SW], w2 = pc[(r0 + 2) * S::SW], w3 = pc[(r0 + 3) * S::SW];
-            const dd d1 = w2 - w1, d2 = w3 - w2;
+            const dd d1 = norm_lim<Lim>(w2 - w1), d2 = norm_lim<Lim>(w3 - w2);
             yw[q] = w3;
             yd[q] = d2;
             ym[q] = slope_dd<Lim>(d2, d1);
@@ -216,7 +224,7 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
             const int L = lane < 12 ? lane : 0;
             const int q = L < 4 ? 2 * L : L + 4;
             const dd *row = tile + q * S::PL + (r + 2) * S::SW;    // smem column = x - x0 + HX
-            edgeD = row[kTmaTX + S::HX] - row[kTmaTX + S::HX - 1];
+            edgeD = norm_lim<Lim>(row[kTmaTX + S::HX] - row[kTmaTX + S::HX - 1]);
             if (Lim == 0) {
                 const int c0 = tsgn_x(q) > 0 ? 0 : kTmaTX + S::HX - 1;
                 edgeS = mc2(row[c0 + 1] - row[c0], row[c0 + 2] - row[c0 + 1]);
@@ -248,7 +256,7 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
                 // mc2(D(x), D(x+1)); the neighbours' values by shuffles, those one column
                 // outside the warp from the duty lane of this population
                 const int duty = q < 8 ? q >> 1 : q - 4;
-                const dd D = f[q] - p[q * S::PL - 1];
+                const dd D = norm_lim<Lim>(f[q] - p[q * S::PL - 1]);
                 dd Dr = shfl_down_dd(D);
                 const dd eD = shfl_dd(edgeD, duty);
                 if (lane == kTmaTX - 1) Dr = eD;
@@ -257,7 +265,7 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
                 } else if (Lim == 1) {
                     tx = sx > 0 ? D + scale2(C.hh[shell], 2.0f) * (Dr - D) : (-Dr) + scale2(C.hh[shell], 2.0f) * ((-D) - (-Dr));
                 } else {
-                    const dd Sx = mc2(D, Dr);
+                    const dd Sx = mc2n(D, Dr);
                     const dd eS = shfl_dd(edgeS, duty);
                     if (sx > 0) {
                         // upwind slope S(x - 1): from lane - 1, at lane 0 from the duty lane
@@ -276,7 +284,7 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
             if (sy != 0) {
                 const dd *pc = tile + q * S::PL + (lane + S::HX);
                 const dd wn = pc[(r + (sy > 0 ? 3 : 4)) * S::SW];
-                const dd dn = wn - yw[q];
+                const dd dn = norm_lim<Lim>(wn - yw[q]);
                 if (sy > 0) {
                     const dd mn = slope_dd<Lim>(yd[q], dn);
                     tyv = Lim == 2 ? yd[q] : yd[q] + C.hhy[shell] * (mn - ym[q]);
