@@ -66,8 +66,8 @@ TRAFFIC_PER_CELL = {
            "sha": "a2afc1f726475ef7"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
-# float64 kernel, counted by ncu on the same sources (profiles/k_step_dd_f64_shear_layer.md);
-# None when the sources changed since.
+# float64 kernel on 32 x 32 tiles, counted by ncu on the same sources
+# (profiles/k_step_dd_f64_shear_layer.md); None when the sources changed since.
 DD_FP32_OPS = {"ops": 3761.3, "sha": "a2afc1f726475ef7"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
@@ -85,7 +85,7 @@ def traffic_per_launch(mode: str, cells: int, kernel: str):
     """ncu DRAM bytes of one fused-step launch scaled to `cells`, or None when the captured
     kernel is not the one that ran or its sources changed since the capture."""
     t = TRAFFIC_PER_CELL.get(mode)
-    want = {"f32": "k_step_tma<", "f64": "k_step_stream<", "dd": "k_step_dd<"}[mode]
+    want = {"f32": "k_step_tma<", "f64": "k_step_stream<", "dd": "k_step_dd<MC>"}[mode]
     if not t or not t["bytes"] or not kernel.startswith(want) or kernel_sources_sha(t["sources"]) != t["sha"]:
         return None
     return t["bytes"] * cells
@@ -111,7 +111,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-kernel", type=int, default=0,
                     help="lbm_options.step_kernel (0 = automatic, 1/3/4/7 plain, 2 TMA tiles, 5 streaming, "
-                         "6 double-buffered TMA tiles)")
+                         "6 double-buffered TMA tiles, 8/9 double-float 32x32/32x4 tiles)")
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving measurement (0 = skip)")
     ap.add_argument("--serving-steps", type=int, default=1000)
@@ -230,7 +230,7 @@ def pinned_like(a):
 # ------------------------------------------------------------------------- GPU arm
 KERNEL_NAMES = {1: "k_step<{r},{d},MC,256>", 2: "k_step_tma<{r},{d},MC>", 3: "k_step<{r},{d},MC,128>",
                 4: "k_step<{r},{d},MC,512>", 5: "k_step_stream<{r},{d},MC>", 6: "k_step_tma_pipe<{r},{d},MC>",
-                7: "k_step<{r},{d},MC,64>", 8: "k_step_dd<MC>"}
+                7: "k_step<{r},{d},MC,64>", 8: "k_step_dd<MC>", 9: "k_step_dd<MC,32x4>"}
 
 
 def run_mode(lbm, p, precision, steps, warmup, device, world, step_kernel=0):
@@ -401,7 +401,7 @@ def fp64_line(lbm, p, args, device, world, hbm):
         sms = torch.cuda.get_device_properties(device).multi_processor_count
         mhz = clocks.get("sm_mhz") or 2070.0
         peak32 = sms * FP32_LANES_PER_SM * mhz * 1e6
-        per_cell = dd_fp32_ops_per_cell()
+        per_cell = dd_fp32_ops_per_cell() if r64["kernel"] == KERNEL_NAMES[8] else None
         ach = per_cell * cells / (r64["step_kernel_ms"] * 1e-3) if per_cell else None
         roof = {"bound": "alu", "achieved": ach / 1e12 if ach else None, "peak": peak32 / 1e12,
                 "unit": "T fp32-op/s", "frac": ach / peak32 if ach else None,
@@ -585,7 +585,7 @@ def config_gpu(lbm, p, precision, steps, warmup, device, hbm, peak_ops=None):
             import torch
             sms = torch.cuda.get_device_properties(device).multi_processor_count
             peak32 = sms * FP32_LANES_PER_SM * 2070.0 * 1e6
-            per_cell = dd_fp32_ops_per_cell()
+            per_cell = dd_fp32_ops_per_cell() if kern == KERNEL_NAMES[8] else None
             ach = per_cell * cells / (k_ms * 1e-3) if per_cell else None
             out["roofline"] = {"bound": "alu", "achieved": ach / 1e12 if ach else None, "peak": peak32 / 1e12,
                                "unit": "T fp32-op/s", "frac": ach / peak32 if ach else None,

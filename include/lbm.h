@@ -94,7 +94,8 @@ typedef struct {
     const lbm_allocator *allocator;/* NULL = cudaMalloc / cudaFree */
     int device;                    /* CUDA device ordinal; < 0 = the current device */
     int step_kernel;               /* fused-step kernel: 0 = automatic (float64: the double-float
-                                      kernel 8 on grids of at least 32 x 32; narrower grids:
+                                      kernel 8 on grids of at least 32 x 32, 9 on grids of 32
+                                      columns or more and 4 to 31 rows; narrower grids:
                                       streaming on grids that give every SM at least 32 rows of a
                                       256-column strip and have at least 4M cells, else plain
                                       64-cell tiles;
@@ -113,7 +114,9 @@ typedef struct {
                                       with the step's arithmetic in double-float form (pairs of
                                       float32, about 2^-47 rounding per operation) on the float32
                                       pipe, populations still stored and returned in float64
-                                      (grids of at least 32 x 32); all agree to round-off of
+                                      (grids of at least 32 x 32), 9 = LBM_FP64 only: the same
+                                      arithmetic on 32 x 4 tiles, two CTAs per SM (grids of at
+                                      least 32 columns and 4 rows); all agree to round-off of
                                       their arithmetic (see lbm_autotune) */
     double dy;                     /* grid spacing along y; <= 0 means dy = dx.  The y projection
                                       of the convection uses the Courant numbers |v_iy| dt / dy and
@@ -199,8 +202,8 @@ int lbm_peak_fp64(int device, double *flops);
 
 /* Pick the fastest fused-step kernel for this context's grid: times `reps` launches of
    each candidate (plain 32 x 4, 32 x 8, 32 x 16 and 64-cell tiles; TMA-staged tiles, the
-   streaming kernel and the double-buffered TMA-staged kernel when the grid and precision
-   allow) on the context's current state, writing the spare buffer without advancing the
+   streaming kernel, the double-buffered TMA-staged kernel and the double-float kernels on
+   32 x 32 and 32 x 4 tiles when the grid and precision allow) on the context's current state, writing the spare buffer without advancing the
    state, and keeps the fastest for later lbm_step calls.  *choice (may be NULL) receives
    the lbm_options.step_kernel code of the winner.  Synchronous.  Not part of the paper's
    method: a throughput tool. */
@@ -212,10 +215,10 @@ int lbm_autotune(lbm_ctx *ctx, int reps, int *choice);
    stream, and stay alive while the batch exists.  Each step of lbm_batch_step runs, per
    group of contexts with the same precision and limiter, one batched ghost-fill launch and
    fused-step launches over the tiles of the group's grids:
-   - contexts whose step kernel is the TMA-staged tile kernel (float32) or the double-float
-     kernel (float64), i.e. the automatic choice on grids of at least 32 x 32 (float64) or
-     32 x 16 (float32), have their tiles in one launch of that kernel's batched form per 128
-     such grids (one CTA per tile; the launch's parameters hold each grid's tensor map,
+   - contexts whose step kernel is the TMA-staged tile kernel (float32) or a double-float
+     kernel (float64), i.e. the automatic choice on grids of at least 32 x 16 (float32) or
+     32 x 4 (float64), have their tiles in one launch of that kernel's batched form per 128
+     such grids (float64: one for the 32 x 32 tiles, one for the 32 x 4 tiles) (one CTA per tile; the launch's parameters hold each grid's tensor map,
      output buffer and tile count, and the CTA stages its grid's coefficients in shared
      memory), with the arithmetic of the single-grid kernel, bit for bit;
    - the other grids share the packed plain kernel, whose persistent CTAs walk a tile list
@@ -273,7 +276,7 @@ int lbm_totals_noalloc(const double *f, int nx, int ny, double dx, double dy, vo
 /* Steps taken since the last lbm_init / lbm_set_state. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* The lbm_options.step_kernel code (1 .. 8) of the fused-step kernel this context runs
+/* The lbm_options.step_kernel code (1 .. 9) of the fused-step kernel this context runs
    (after automatic selection or lbm_autotune); -1 for a NULL context. */
 int lbm_step_kernel(const lbm_ctx *ctx);
 

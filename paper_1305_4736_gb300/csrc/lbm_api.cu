@@ -47,11 +47,13 @@ struct lbm_ctx {
     bool use_stream = false;
     bool use_pipe = false;
     bool use_dd = false;          // float64 mode in double-float arithmetic (step_kernel 8)
-    lbm::Coef<lbm::dd> cdd{};     // its coefficients
+    bool use_ddn = false;         // the same on narrow tiles of 32 x 4 (step_kernel 9)
+    lbm::Coef<lbm::dd> cdd{};     // their coefficients
     int plain_ty = lbm::kTY;      // tile height of the plain step kernel
     CUtensorMap tmap[2];          // tile-copy descriptors of the two population buffers
     CUtensorMap smap[2];          // row-copy descriptors (streaming kernel)
     CUtensorMap pmap[2];          // tile-copy descriptors of the double-buffered kernel
+    CUtensorMap nmap[2];          // tile-copy descriptors of the narrow double-float tiles
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0, dy = 0.0;
@@ -267,6 +269,13 @@ bool make_tile_maps(lbm_ctx *c)
            make_tensor_map(&c->tmap[1], c->f[1], c->P, c->prec, sw, sh);
 }
 
+bool make_narrow_maps(lbm_ctx *c)
+{
+    const int sw = lbm::DdNarrowShape::SW, sh = lbm::DdNarrowShape::SH;
+    return make_tensor_map(&c->nmap[0], c->f[0], c->P, c->prec, sw, sh) &&
+           make_tensor_map(&c->nmap[1], c->f[1], c->P, c->prec, sw, sh);
+}
+
 bool make_row_maps(lbm_ctx *c)
 {
     using S = lbm::StreamShape<float>;
@@ -304,10 +313,20 @@ bool dd_ready(lbm_ctx *c)
     return make_tile_maps(c);
 }
 
+// The double-float kernel on narrow tiles (grids of 4 to 31 rows): their maps and the Coef<dd>.
+bool ddn_ready(lbm_ctx *c)
+{
+    if (c->prec != LBM_FP64 || !lbm::dd_narrow_supported(c->P) || lbm::dd_prepare() != cudaSuccess) return false;
+    lbm::coef_dd(c->P, &c->cdd);
+    return make_narrow_maps(c);
+}
+
 // One fused step of context c from buffer `in` into buffer in ^ 1, on stream st.
 cudaError_t launch_fused_step(lbm_ctx *c, int in, cudaStream_t st)
 {
     if (c->use_dd) return lbm::launch_step_dd(c->P, &c->cdd, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
+    if (c->use_ddn)
+        return lbm::launch_step_dd(c->P, &c->cdd, &c->nmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st, true);
     if (c->use_pipe) return lbm::launch_step_tma_pipe(c->P, &c->pmap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_stream) return lbm::launch_step_stream(c->P, c->prec, &c->smap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
@@ -487,22 +506,35 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     c->tma_err = c->flag + 1;
     c->init_err = c->flag + 2;
     int want = opt ? opt->step_kernel : 0;
-    if (want < 0 || want > 8) {
+    if (want < 0 || want > 9) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "unknown step_kernel");
     }
     if (want == 3) c->plain_ty = 4;
     if (want == 4) c->plain_ty = 16;
     if (want == 7) c->plain_ty = 2;
-    // automatic, float64: the double-float kernel wherever its 32 x 32 tiles fit (on GB300 the
-    // float32 pipe runs its arithmetic 2-2.5x faster than the float64 kernels run theirs, from
-    // 256 x 256 cells up); on narrower grids the float64 pipe (about 1.6 lane operations per
-    // cycle per SM): the streaming kernel when the grid gives every SM at least 32 rows of a
-    // 256-column strip; else the plain kernel, on 256-cell tiles when they still give every SM
-    // four tiles (their flow-velocity ring costs less), on 64-cell tiles below that, which
-    // spread a small grid's float64 work over more SMs
-    if (want == 0 && prec == LBM_FP64 && dd_ready(c)) want = 8;
-    cudaGetLastError();
+    // automatic, float64: the double-float kernels (on GB300 the float32 pipe runs their
+    // arithmetic 2.5x faster than the float64 kernels run theirs) wherever their tiles fit; on
+    // grids narrower than 32 columns or lower than 4 rows the float64 pipe (about 1.6 lane
+    // operations per cycle per SM): the streaming kernel when the grid gives every SM at least
+    // 32 rows of a 256-column strip; else the plain kernel, on 256-cell tiles when they still
+    // give every SM four tiles (their flow-velocity ring costs less), on 64-cell tiles below
+    // that, which spread a small grid's float64 work over more SMs.  The double-float kernel
+    // runs on 32 x 32 tiles where the grid has at least two thirds of a wave of them (one CTA
+    // per SM); on smaller grids, and on grids of 4 to 31 rows, on 32 x 4 tiles (two CTAs per
+    // SM): a 32 x 32 tile takes about 44 us on its SM, so a small grid finishes sooner in more,
+    // shorter tiles (128 x 96: 17 us against 44 us a step)
+    if (want == 0 && prec == LBM_FP64) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (sms < 1) sms = 152;
+        const long long tiles = (long long)((nx + lbm::kTmaTX - 1) / lbm::kTmaTX) *
+                                ((ny + lbm::TmaShape<double>::TR - 1) / lbm::TmaShape<double>::TR);
+        if (3 * tiles >= 2LL * sms && dd_ready(c)) want = 8;
+        cudaGetLastError();
+        if (want == 0 && ddn_ready(c)) want = 9;
+        cudaGetLastError();
+    }
     if (want == 0 && prec == LBM_FP64) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -524,6 +556,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     // extra loads in edge tiles cost less than the ghost columns' copy; on smaller grids a
     // kernel lasts as long as its slowest tiles, which the extra loads lengthen
     if (want == 8 && dd_ready(c)) c->use_dd = true;
+    if (want == 9 && ddn_ready(c)) c->use_ddn = true;
     if ((c->use_tma || c->use_dd) && bc->xlo.kind == LBM_BC_PERIODIC) {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -532,7 +565,7 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
     }
     if (want == 6 && pipe_ready(c)) c->use_pipe = true;
     if ((want == 2 && !c->use_tma) || (want == 5 && !c->use_stream) || (want == 6 && !c->use_pipe) ||
-        (want == 8 && !c->use_dd)) {
+        (want == 8 && !c->use_dd) || (want == 9 && !c->use_ddn)) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ARG, "requested step kernel unavailable for this grid or driver");
     }
@@ -925,8 +958,8 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
     // candidates: 1 = plain 32x8, 3 = plain 32x4, 4 = plain 32x16, 7 = plain 64-cell tiles,
     // 2 = TMA-staged, 5 = streaming, 6 = double-buffered TMA-staged 32x16 (float32),
-    // 8 = double-float TMA-staged (float64)
-    int cands[8] = {1, 3, 4, 7, 0, 0, 0, 0};
+    // 8 = double-float TMA-staged (float64), 9 = the same on 32 x 4 tiles
+    int cands[10] = {1, 3, 4, 7, 0, 0, 0, 0, 0, 0};
     int ncand = 4;
     const bool tma_ok = c->use_tma || tma_ready(c);
     cudaGetLastError();
@@ -940,6 +973,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     const bool dd_ok = c->use_dd || dd_ready(c);
     cudaGetLastError();
     if (dd_ok) cands[ncand++] = 8;
+    const bool ddn_ok = c->use_ddn || ddn_ready(c);
+    cudaGetLastError();
+    if (ddn_ok) cands[ncand++] = 9;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "cudaEventCreate");
@@ -950,6 +986,9 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     for (int k = 0; k < ncand && ce == cudaSuccess; k++) {
         auto run = [&]() {
             const int cd = cands[k];
+            if (cd == 9)
+                return lbm::launch_step_dd(c->P, &c->cdd, &c->nmap[c->cur], c->f[c->cur], c->f[c->cur ^ 1],
+                                           c->tma_err, c->stream, true);
             if (cd == 8)
                 return lbm::launch_step_dd(c->P, &c->cdd, &c->tmap[c->cur], c->f[c->cur], c->f[c->cur ^ 1],
                                            c->tma_err, c->stream);
@@ -981,6 +1020,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     c->use_stream = best_c == 5;
     c->use_pipe = best_c == 6;
     c->use_dd = best_c == 8;
+    c->use_ddn = best_c == 9;
     c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : (best_c == 7 ? 2 : 8));
     if (choice) *choice = best_c;
     return LBM_OK;
@@ -992,6 +1032,7 @@ int lbm_step_kernel(const lbm_ctx *c)
 {
     if (!c) return -1;
     if (c->use_dd) return 8;
+    if (c->use_ddn) return 9;
     if (c->use_pipe) return 6;
     if (c->use_stream) return 5;
     if (c->use_tma) return 2;
@@ -1017,6 +1058,7 @@ struct lbm_batch {
         // batched TMA-staged kernel: the members it serves (indices into members, in launch
         // order) and their TileGrid blocks (Coef<float> or Coef<dd> by precision)
         std::vector<int> tk;
+        std::vector<int> tkn;                    // float64 members on narrow 32 x 4 tiles
         void *tblock = nullptr;
         size_t tbytes = 0;
         int ntt = 0;                             // tiles per step
@@ -1051,21 +1093,24 @@ cudaError_t batch_upload_cur(lbm_batch *b)
     return cudaSuccess;
 }
 
-// The group's batched TMA-staged launches (kTmaBatchGrids grids each), with every member's
-// input map, output buffer and flag resolved for this step's parity.
-cudaError_t batch_launch_tma(lbm_batch *b, const lbm_batch::Group &g, int phase, cudaStream_t st)
+// The group's batched TMA-staged launches (kTmaBatchGrids grids each) over the members `tk`
+// (float32 tile kernel, or float64 double-float kernel on 32 x 32 tiles) and, in float64, over
+// the members `tkn` on narrow 32 x 4 tiles, with every member's input map, output buffer and flag
+// resolved for this step's parity.  The group's TileGrid table holds tk's blocks, then tkn's.
+cudaError_t batch_launch_tma_list(lbm_batch *b, const lbm_batch::Group &g, const std::vector<int> &list, bool narrow,
+                                  const char *tg0, int phase, cudaStream_t st)
 {
     static thread_local lbm::TmaBatchArgs A;
     const bool f64 = g.prec == LBM_FP64;
-    const int tr = f64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR;
+    const int tr = narrow ? lbm::DdNarrowShape::TR : (f64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR);
     const size_t tgb = f64 ? sizeof(lbm::TileGrid<lbm::Coef<lbm::dd>>) : sizeof(lbm::TileGrid<lbm::Coef<float>>);
-    for (size_t c0 = 0; c0 < g.tk.size(); c0 += lbm::kTmaBatchGrids) {
-        const int n = (int)std::min<size_t>(lbm::kTmaBatchGrids, g.tk.size() - c0);
+    for (size_t c0 = 0; c0 < list.size(); c0 += lbm::kTmaBatchGrids) {
+        const int n = (int)std::min<size_t>(lbm::kTmaBatchGrids, list.size() - c0);
         int tiles = 0;
         for (int k = 0; k < n; k++) {
-            const lbm_ctx *c = b->ctxs[g.members[g.tk[c0 + k]]];
+            const lbm_ctx *c = b->ctxs[g.members[list[c0 + k]]];
             const int in = c->cur ^ phase;
-            A.map[k] = c->tmap[in];
+            A.map[k] = narrow ? c->nmap[in] : c->tmap[in];
             A.out[k] = c->f[in ^ 1];
             A.err[k] = c->tma_err;
             A.first[k] = tiles;
@@ -1074,13 +1119,23 @@ cudaError_t batch_launch_tma(lbm_batch *b, const lbm_batch::Group &g, int phase,
         }
         A.first[n] = tiles;
         A.n = n;
-        const char *tg = (const char *)g.tblock + c0 * tgb;
+        const char *tg = tg0 + c0 * tgb;
         const cudaError_t ce =
-            f64 ? lbm::launch_step_dd_batch(A, (const lbm::TileGrid<lbm::Coef<lbm::dd>> *)tg, g.limiter, st)
+            f64 ? lbm::launch_step_dd_batch(A, (const lbm::TileGrid<lbm::Coef<lbm::dd>> *)tg, g.limiter, narrow, st)
                 : lbm::launch_step_tma_batch(A, (const lbm::TileGrid<lbm::Coef<float>> *)tg, g.limiter, st);
         if (ce != cudaSuccess) return ce;
     }
     return cudaSuccess;
+}
+
+cudaError_t batch_launch_tma(lbm_batch *b, const lbm_batch::Group &g, int phase, cudaStream_t st)
+{
+    const char *tg = (const char *)g.tblock;
+    cudaError_t ce = batch_launch_tma_list(b, g, g.tk, false, tg, phase, st);
+    if (ce == cudaSuccess && !g.tkn.empty())
+        ce = batch_launch_tma_list(b, g, g.tkn, true, tg + g.tk.size() * sizeof(lbm::TileGrid<lbm::Coef<lbm::dd>>),
+                                   phase, st);
+    return ce;
 }
 
 cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
@@ -1099,7 +1154,7 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
     for (auto &g : b->groups) {
         ce = lbm::launch_step_batch(g.dP, g.dG, g.dT, g.ntiles, g.prec, g.limiter, g.nt,
                                     g.nt == lbm::kBatchThreadsFp64 ? 2 * b->ctas : b->ctas, phase, st);
-        if (ce == cudaSuccess && !g.tk.empty()) ce = batch_launch_tma(b, g, phase, st);
+        if (ce == cudaSuccess && (!g.tk.empty() || !g.tkn.empty())) ce = batch_launch_tma(b, g, phase, st);
         if (ce != cudaSuccess) return ce;
     }
     for (size_t j = 0; j < b->solo.size(); j++) {
@@ -1121,7 +1176,7 @@ cudaError_t batch_launch_step(lbm_batch *b, int phase, cudaStream_t st)
 // several such kernels share the SMs); the other grids share the packed plain tile kernel.
 bool batch_tma(const lbm_ctx *c)
 {
-    return (c->prec == LBM_FP32_DEV && c->use_tma) || (c->prec == LBM_FP64 && c->use_dd);
+    return (c->prec == LBM_FP32_DEV && c->use_tma) || (c->prec == LBM_FP64 && (c->use_dd || c->use_ddn));
 }
 
 bool batch_solo(const lbm_ctx *c, int sms)
@@ -1156,6 +1211,15 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (ce != cudaSuccess) { delete b; return cuda_fail(nullptr, ce, "device query"); }
     b->ctas = 4 * sms;
+    // a float64 member on narrow double-float tiles whose grid takes 32 x 32 tiles steps on those
+    // in the batch (the same bits: the two shapes run the same operations on every value; spread
+    // over a batch, the larger tiles cost less per cell)
+    std::vector<char> wide(n, 0);
+    for (int i = 0; i < n; i++) {
+        lbm_ctx *c = ctxs[i];
+        wide[i] = c->use_dd || (c->use_ddn && lbm::tma_supported(c->P, LBM_FP64) && make_tile_maps(c));
+    }
+    cudaGetLastError();
     for (int i = 0; i < n; i++) {
         const lbm_ctx *c = ctxs[i];
         const bool tma = batch_tma(c);
@@ -1186,7 +1250,7 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
         std::vector<int4> tiles;
         std::vector<lbm::Params> hp;
         std::vector<lbm::TileGrid<lbm::Coef<float>>> htf;
-        std::vector<lbm::TileGrid<lbm::Coef<lbm::dd>>> htd;
+        std::vector<lbm::TileGrid<lbm::Coef<lbm::dd>>> htd, htdn;   // float64: 32 x 32 members, narrow ones
         const int tr = g.prec == LBM_FP64 ? lbm::TmaShape<double>::TR : lbm::TmaShape<float>::TR;
         for (size_t k = 0; k < g.members.size(); k++) {
             const lbm_ctx *c = b->ctxs[g.members[k]];
@@ -1195,11 +1259,14 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->tma_err, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
             if (g.tma[k]) {
-                g.tk.push_back((int)k);
-                g.ntt += ((c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX) * ((c->P.ny + tr - 1) / tr);
+                const bool narrow = g.prec == LBM_FP64 && !wide[g.members[k]];
+                const int trk = narrow ? lbm::DdNarrowShape::TR : tr;
+                (narrow ? g.tkn : g.tk).push_back((int)k);
+                g.ntt += ((c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX) * ((c->P.ny + trk - 1) / trk);
                 if (g.prec == LBM_FP64)
-                    htd.push_back(lbm::TileGrid<lbm::Coef<lbm::dd>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
-                                                                    c->P.plane, 0, c->cdd});
+                    (narrow ? htdn : htd)
+                        .push_back(lbm::TileGrid<lbm::Coef<lbm::dd>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
+                                                                     c->P.plane, 0, c->cdd});
                 else
                     htf.push_back(lbm::TileGrid<lbm::Coef<float>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
                                                                   c->P.plane, 0, c->P.cf});
@@ -1228,7 +1295,8 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             ce = cudaMemcpyAsync(g.dG, g.hG.data(), g.hG.size() * sizeof(lbm::BatchGrid), cudaMemcpyHostToDevice,
                                  b->stream);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(g.dT, tiles.data(), nt, cudaMemcpyHostToDevice, b->stream);
-        if (ce == cudaSuccess && !g.tk.empty()) {
+        htd.insert(htd.end(), htdn.begin(), htdn.end());   // table order: tk, then tkn
+        if (ce == cudaSuccess && (!htd.empty() || !htf.empty())) {
             const void *src = htd.empty() ? (const void *)htf.data() : (const void *)htd.data();
             g.tbytes = htd.empty() ? htf.size() * sizeof(htf[0]) : htd.size() * sizeof(htd[0]);
             g.tblock = b->alloc.alloc(g.tbytes, b->stream, b->alloc.user);

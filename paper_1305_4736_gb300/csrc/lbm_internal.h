@@ -80,6 +80,23 @@ struct TmaShape {
     static constexpr size_t smem_bytes = tile_bytes + sizeof(R) * (sizeof(R) == sizeof(float) ? 2 : 3) * UW * UH;
 };
 bool tma_supported(const Params &P, int prec);
+// Narrow tiles of the double-float float64 kernel (step_kernel 9): 4 warps, 32 x 4 tiles, one
+// row per thread, two CTAs per SM, for grids of 4 to 31 rows (and 32 columns or more), where the
+// 32 x 32 tiles do not fit.  The staged tile is that of TmaShape<double> with 8 rows.
+struct DdNarrowShape {
+    static constexpr int TT = 4;
+    static constexpr int CTAS = 2;
+    static constexpr int KR = 1;
+    static constexpr int TR = TT * KR;
+    static constexpr int HX = 2;
+    static constexpr int SW = kTmaTX + 2 * HX;
+    static constexpr int SH = TR + 4;
+    static constexpr int PL = SW * SH;
+    static constexpr int UW = kTmaTX + 2, UH = TR + 2;
+    static constexpr size_t tile_bytes = sizeof(double) * NQ * PL;
+    static constexpr size_t smem_bytes = tile_bytes + sizeof(double) * 3 * UW * UH;
+};
+bool dd_narrow_supported(const Params &P);
 // Batched TMA-staged steps over the tiles of up to kTmaBatchGrids grids of a batch group, one
 // CTA per tile of kTmaTX x TmaShape<R>::TR cells: grid k owns the launch's tiles first[k] ..
 // first[k+1] - 1, row by row, ntx[k] to a row.  A CTA finds its grid and tile from blockIdx
@@ -106,7 +123,9 @@ struct TileGrid {
 };
 cudaError_t launch_step_tma_batch(const TmaBatchArgs &A, const TileGrid<Coef<float>> *tg, int limiter,
                                   cudaStream_t st);
-cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, cudaStream_t st);
+// narrow: tiles of DdNarrowShape (the grids' maps have its box), else of TmaShape<double>.
+cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, bool narrow,
+                                 cudaStream_t st);
 // Failure-path check of the bounded mbarrier waits (lbm_wait_selftest): *flag = 1 when the
 // wait on a phase that nothing completes gave up at its limit; *ms = the kernel's duration.
 cudaError_t wait_selftest(int *flag, float *ms);
@@ -158,11 +177,12 @@ cudaError_t launch_step_stream(const Params &P, int prec, const void *tmap, void
 
 // Float64-mode step in double-float arithmetic on the float32 pipe (step_kernel 8): the tiles
 // and tensor maps of the float64 TMA-staged kernel; `coef` is the Coef<dd> of the context
-// (coef_dd).
+// (coef_dd).  narrow (step_kernel 9): the tiles of DdNarrowShape, `tmap` with its box, no x
+// wrap in the kernel.
 void coef_dd(const Params &P, Coef<dd> *out);
 cudaError_t dd_prepare();
 cudaError_t launch_step_dd(const Params &P, const void *coef, const void *tmap, const void *fin, void *fout,
-                           int *err, cudaStream_t st);
+                           int *err, cudaStream_t st, bool narrow = false);
 
 // Sustained float64 FMA rate of the current device in FLOP/s (FMA = 2).
 cudaError_t measure_fp64_fma(double *flops);

@@ -151,11 +151,11 @@ __device__ __forceinline__ dd slope_dd(dd a, dd b)
 // shared memory (smraw) is split, then phases 1 and 2 produce the tile's new float64 values.
 // ---------------------------------------------------------------------------
 // P: the context's Params, or the TileGrid block of a batched launch (nx, ny, pitch, plane).
-template <int Lim, bool C9, typename PP>
+// S: the tile shape (TmaShape<double> or DdNarrowShape).
+template <int Lim, bool C9, typename S, typename PP>
 __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned char *smraw,
                                         double *__restrict__ fout, int x0, int y0)
 {
-    using S = TmaShape<double>;
     double *tile64 = reinterpret_cast<double *>(smraw);
     dd *tile = reinterpret_cast<dd *>(smraw);
     dd *su = tile + NQ * S::PL;
@@ -311,12 +311,11 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
 // The single-grid kernel.  Shape as the float64 TMA-staged kernel: 8 warps, 32 x 32 tiles,
 // 4 rows per thread, one CTA per SM (the staged tile takes 162 KB).
 // ---------------------------------------------------------------------------
-template <int Lim, bool Wrap, bool C9>
-__global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
+template <int Lim, bool Wrap, bool C9, typename S = TmaShape<double>>
+__global__ void __launch_bounds__(kTmaTX * S::TT, S::CTAS)
 k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, const __grid_constant__ CUtensorMap tm,
           const double *__restrict__ fin, double *__restrict__ fout, int *err)
 {
-    using S = TmaShape<double>;
     extern __shared__ __align__(128) unsigned char smraw[];
     double *tile64 = reinterpret_cast<double *>(smraw);
     __shared__ __align__(8) unsigned long long bar;
@@ -354,7 +353,7 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
         wrap_halo<double>(P, fin, tile64, x0, y0, tid, kThreads);
         __syncthreads();
     }
-    dd_tile<Lim, C9>(P, C, smraw, fout, x0, y0);
+    dd_tile<Lim, C9, S>(P, C, smraw, fout, x0, y0);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,11 +364,10 @@ k_step_dd(const __grid_constant__ Params P, const __grid_constant__ Coef<dd> C, 
 // correction runs for every grid; its factors are zero where s8 = s5, which leaves the
 // residuals unchanged bit for bit.
 // ---------------------------------------------------------------------------
-template <int Lim>
-__global__ void __launch_bounds__(kTmaTX * TmaShape<double>::TT, 1)
+template <int Lim, typename S = TmaShape<double>>
+__global__ void __launch_bounds__(kTmaTX * S::TT, S::CTAS)
 k_step_dd_batch(const __grid_constant__ TmaBatchArgs A, const TileGrid<Coef<dd>> *__restrict__ TG)
 {
-    using S = TmaShape<double>;
     using T = TileGrid<Coef<dd>>;
     static_assert(sizeof(T) % 16 == 0, "TileGrid copy");
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -398,7 +396,7 @@ k_step_dd_batch(const __grid_constant__ TmaBatchArgs A, const TileGrid<Coef<dd>>
         }
         return;
     }
-    dd_tile<Lim, true>(Ts, Ts.cf, smraw, static_cast<double *>(A.out[g]), x0, y0);
+    dd_tile<Lim, true, S>(Ts, Ts.cf, smraw, static_cast<double *>(A.out[g]), x0, y0);
 }
 
 // Coefficients in double-float from the float64 tables (host).
@@ -410,47 +408,69 @@ void coef_dd(const Params &P, Coef<dd> *out)
     for (size_t k = 0; k < sizeof(Coef<double>) / sizeof(double); k++) dst[k] = dd_host(src[k]);
 }
 
-template <int Lim, bool Wrap>
+template <int Lim, bool Wrap, typename S>
 static void launch_dd_lim(const Params &P, const Coef<dd> &C, const CUtensorMap &tm, const double *a, double *b,
                           int *err, cudaStream_t st)
 {
-    using S = TmaShape<double>;
     const dim3 block(kTmaTX, S::TT);
     const dim3 grid((P.nx + kTmaTX - 1) / kTmaTX, (P.ny + S::TR - 1) / S::TR);
-    if (P.has_c9) k_step_dd<Lim, Wrap, true><<<grid, block, S::smem_bytes, st>>>(P, C, tm, a, b, err);
-    else k_step_dd<Lim, Wrap, false><<<grid, block, S::smem_bytes, st>>>(P, C, tm, a, b, err);
+    if (P.has_c9) k_step_dd<Lim, Wrap, true, S><<<grid, block, S::smem_bytes, st>>>(P, C, tm, a, b, err);
+    else k_step_dd<Lim, Wrap, false, S><<<grid, block, S::smem_bytes, st>>>(P, C, tm, a, b, err);
+}
+
+bool dd_narrow_supported(const Params &P)
+{
+    using S = DdNarrowShape;
+    return P.pitch >= S::SW && P.ny + 4 >= S::SH && P.nx >= kTmaTX;
 }
 
 cudaError_t launch_step_dd(const Params &P, const void *coef, const void *tmap, const void *fin, void *fout,
-                           int *err, cudaStream_t st)
+                           int *err, cudaStream_t st, bool narrow)
 {
+    using W = TmaShape<double>;
+    using N = DdNarrowShape;
     const CUtensorMap &tm = *reinterpret_cast<const CUtensorMap *>(tmap);
     const Coef<dd> &C = *reinterpret_cast<const Coef<dd> *>(coef);
     const double *a = (const double *)fin;
     double *b = (double *)fout;
+    if (narrow) {
+        // the ghost fill writes every ghost cell of a context on narrow tiles: no x wrap
+        if (P.limiter == 0) launch_dd_lim<0, false, N>(P, C, tm, a, b, err, st);
+        else if (P.limiter == 1) launch_dd_lim<1, false, N>(P, C, tm, a, b, err, st);
+        else launch_dd_lim<2, false, N>(P, C, tm, a, b, err, st);
+        return cudaGetLastError();
+    }
     const bool wrap = (P.wrap & 1) != 0;
     if (P.limiter == 0) {
-        if (wrap) launch_dd_lim<0, true>(P, C, tm, a, b, err, st);
-        else launch_dd_lim<0, false>(P, C, tm, a, b, err, st);
+        if (wrap) launch_dd_lim<0, true, W>(P, C, tm, a, b, err, st);
+        else launch_dd_lim<0, false, W>(P, C, tm, a, b, err, st);
     } else if (P.limiter == 1) {
-        if (wrap) launch_dd_lim<1, true>(P, C, tm, a, b, err, st);
-        else launch_dd_lim<1, false>(P, C, tm, a, b, err, st);
+        if (wrap) launch_dd_lim<1, true, W>(P, C, tm, a, b, err, st);
+        else launch_dd_lim<1, false, W>(P, C, tm, a, b, err, st);
     } else {
-        if (wrap) launch_dd_lim<2, true>(P, C, tm, a, b, err, st);
-        else launch_dd_lim<2, false>(P, C, tm, a, b, err, st);
+        if (wrap) launch_dd_lim<2, true, W>(P, C, tm, a, b, err, st);
+        else launch_dd_lim<2, false, W>(P, C, tm, a, b, err, st);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, cudaStream_t st)
+template <typename S>
+static void launch_dd_batch_shape(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, int ntiles,
+                                  cudaStream_t st)
 {
-    using S = TmaShape<double>;
+    const dim3 block(kTmaTX, S::TT);
+    if (limiter == 0) k_step_dd_batch<0, S><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else if (limiter == 1) k_step_dd_batch<1, S><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    else k_step_dd_batch<2, S><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+}
+
+cudaError_t launch_step_dd_batch(const TmaBatchArgs &A, const TileGrid<Coef<dd>> *tg, int limiter, bool narrow,
+                                 cudaStream_t st)
+{
     const int ntiles = A.first[A.n];
     if (ntiles <= 0) return cudaSuccess;
-    const dim3 block(kTmaTX, S::TT);
-    if (limiter == 0) k_step_dd_batch<0><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
-    else if (limiter == 1) k_step_dd_batch<1><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
-    else k_step_dd_batch<2><<<ntiles, block, S::smem_bytes, st>>>(A, tg);
+    if (narrow) launch_dd_batch_shape<DdNarrowShape>(A, tg, limiter, ntiles, st);
+    else launch_dd_batch_shape<TmaShape<double>>(A, tg, limiter, ntiles, st);
     return cudaGetLastError();
 }
 
@@ -476,6 +496,8 @@ cudaError_t dd_prepare()
     set((const void *)k_step_dd_batch<0>);
     set((const void *)k_step_dd_batch<1>);
     set((const void *)k_step_dd_batch<2>);
+    // narrow tiles: within the default 48 KB of dynamic shared memory
+    static_assert(DdNarrowShape::smem_bytes <= 48 * 1024, "narrow tile within the default shared memory");
     return e;
 }
 

@@ -404,5 +404,5 @@ class Solver:
 
     @property
     def step_kernel(self):
-        """lbm_options.step_kernel code of the fused-step kernel in use (1 .. 7)."""
+        """lbm_options.step_kernel code of the fused-step kernel in use (1 .. 9)."""
         return lbm_step_kernel(self.h)

@@ -110,7 +110,7 @@ def test_autotune_keeps_state_and_parity(orc, lbm, prec):
     s.step(10)
     before = s.get_state()
     choice = s.autotune(3)
-    assert choice in (1, 2, 3, 4, 5, 6, 7, 8)
+    assert choice in (1, 2, 3, 4, 5, 6, 7, 8, 9)
     assert s.step_kernel == choice
     assert np.array_equal(s.get_state(), before)
     assert s.step_count == 10
@@ -126,11 +126,12 @@ def test_autotune_keeps_state_and_parity(orc, lbm, prec):
 def test_batch_runs_large_members_on_their_own_kernels(lbm):
     """A float64 1280 x 1024 member on the streaming kernel runs that kernel inside the batch's
     graph, and a float32 640 x 512 member on the tile kernel goes to the batched tile kernel:
-    both bit-identical to stepping them alone.  The Sod member shares the packed plain kernel.
+    both bit-identical to stepping them alone.  The float64 Sod member, on the plain kernel,
+    shares the packed plain kernel.
     Stepping a member alone an odd number of times between batch steps flips its buffer
     parity, and the batch recaptures its graph."""
     specs = [(wl.shear_layer(640, ny=512, seed=3), 1, 0), (wl.shear_layer(1280, ny=1024, seed=4), 0, 5),
-             (wl.sod(200, 4), 0, 0), (wl.shear_layer(96, ny=40, seed=5), 1, 0)]
+             (wl.sod(200, 4), 0, 7), (wl.shear_layer(96, ny=40, seed=5), 1, 0)]
 
     def make():
         out = []
@@ -174,7 +175,22 @@ def _tma_mix():
             (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
     out.append((q, 0, 0))
     out.append((q, 1, 0))
+    # float64 grids of 4 to 31 rows: the double-float kernel on narrow 32 x 4 tiles
+    for k, (nx, ny) in enumerate([(32, 4), (100, 13), (250, 31)]):
+        out.append((wl.shock_interface(nx=nx, ny=ny, steps=1), 0, (0, 1, 2)[k]))
     return out
+
+
+def _tma_kernel(s):
+    """The kernel a member of the TMA-staged mix runs alone: float32 tiles; float64 32 x 32 tiles
+    on grids of at least two thirds of a wave of them, else narrow 32 x 4 tiles (in the batch,
+    every float64 member whose grid takes 32 x 32 tiles steps on those)."""
+    import torch
+    if s.precision == 1:
+        return 2
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = ((s.nx + 31) // 32) * ((s.ny + 31) // 32)
+    return 8 if s.ny >= 32 and 3 * tiles >= 2 * sms else 9
 
 
 def test_batched_tma_kernels_equal_solo_bit_for_bit(lbm):
@@ -185,7 +201,7 @@ def test_batched_tma_kernels_equal_solo_bit_for_bit(lbm):
     batched = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
     solo = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
     for s in batched:
-        assert s.step_kernel == (8 if s.precision == 0 else 2)
+        assert s.step_kernel == _tma_kernel(s)
     b = lbm.Batch(batched)
     b.step(9)
     batched[3].step(1)
@@ -222,4 +238,37 @@ def test_batched_tma_members_against_oracle(orc, lbm):
             du = np.hypot(g[1] - r[1], g[2] - r[2])
             un = np.hypot(r[1], r[2])
             assert du.sum() / un.sum() <= 1e-4 and du.max() / un.max() <= 1e-3, (p.name, p.nx, p.ny, lim)
+        s.close()
+
+
+def test_batched_tma_launches_split_past_the_parameter_block(lbm):
+    """A batch group with more tile-kernel members than one launch's parameter block holds
+    (128 grids) steps them in several launches: 140 float32 grids and 133 float64 grids of
+    one to six tiles each, with different sizes, limiters and seeds, bit-identical to stepping
+    each alone, over a graph replay, an odd step and a member stepped alone in between."""
+    probs = []
+    rng = np.random.default_rng(5)
+    for k in range(140):
+        nx, ny = int(rng.choice([32, 40, 64, 96])), int(rng.choice([16, 20, 32, 48]))
+        probs.append((wl.shear_layer(nx, ny=ny, seed=100 + k), 1, 0))
+    for k in range(133):
+        nx, ny = int(rng.choice([32, 48, 64])), int(rng.choice([32, 40, 64]))
+        probs.append((wl.shear_layer(nx, ny=ny, seed=300 + k), 0, 0))
+    batched = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
+    solo = [_solver(lbm, p, prec, lim, 0) for p, prec, lim in probs]
+    for s in batched:
+        assert s.step_kernel == _tma_kernel(s)
+    b = lbm.Batch(batched)
+    b.step(4)
+    batched[130].step(1)
+    solo[130].step(1)
+    batched[270].step(1)
+    solo[270].step(1)
+    b.step(3)
+    for s in solo:
+        s.step(7)
+    for k, (x, y) in enumerate(zip(batched, solo)):
+        assert np.array_equal(x.get_state(), y.get_state()), (k, probs[k][0].nx, probs[k][0].ny)
+    b.close()
+    for s in batched + solo:
         s.close()

@@ -1,4 +1,5 @@
-"""GPU parity of the double-float float64 kernel (lbm_options.step_kernel = 8).
+"""GPU parity of the double-float float64 kernel (lbm_options.step_kernel = 8, and 9 on narrow
+32 x 4 tiles).
 
 The populations stay float64; the step's arithmetic runs in double-float form on the float32
 pipe (about 2^-47 rounding per operation instead of 2^-53).  The bar is the float64 mode's:
@@ -112,10 +113,13 @@ def test_dd_kernel_reduced_configs_1000_steps(orc, lbm, name):
         assert v <= TOL, f"{k}: {v:.3e} ({errs})"
 
 
-@pytest.mark.parametrize("nx,ny,want", [(256, 256, 8), (33, 32, 8), (31, 64, 7), (200, 4, 7), (4, 200, 7)])
+@pytest.mark.parametrize("nx,ny,want", [(512, 512, 8), (384, 384, 8), (8192, 32, 8), (256, 256, 9), (33, 32, 9),
+                                         (33, 31, 9), (200, 4, 9), (2048, 16, 9), (31, 64, 7), (4, 200, 7),
+                                         (200, 3, 7)])
 def test_automatic_float64_choice(lbm, nx, ny, want):
-    """The double-float kernel is the automatic float64 choice wherever its 32 x 32 tiles fit;
-    narrower grids keep the float64-pipe kernels."""
+    """The automatic float64 choice is the double-float kernel: on 32 x 32 tiles where the grid
+    has at least two thirds of a wave of them (101 on 152 SMs), else on 32 x 4 tiles where those
+    fit (32 columns, 4 rows); grids narrower than that keep the float64-pipe kernels."""
     p = wl.shear_layer(max(nx, ny), ny=ny)
     p.nx = nx
     p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:, :nx]) for a in (p.rho, p.ux, p.uy, p.T))
@@ -135,7 +139,7 @@ def test_dd_kernel_autotune_candidate(lbm):
     s = lbm.Solver.from_problem(p)
     s.init(*p.fields())
     choice = s.autotune(reps=3)
-    assert choice in (1, 2, 3, 4, 5, 7, 8) and s.step_kernel == choice
+    assert choice in (1, 2, 3, 4, 5, 7, 8, 9) and s.step_kernel == choice
     s.close()
 
 
@@ -191,3 +195,65 @@ def test_dd_kernel_conserves_periodic_totals(lbm):
     t1 = s.totals()
     assert np.abs(t1 - t0).max() <= 1e-12 * np.abs(t0).max()
     s.close()
+
+
+# ---- narrow tiles (step_kernel 9): grids of 4 to 31 rows ----
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_narrow_dd_kernel_each_limiter_against_oracle(orc, lbm, limiter):
+    p = wl.shock_interface(nx=150, ny=13, steps=120)          # ragged against 32 x 4 tiles
+    _check(_run(lbm, p, 120, kernel=9, limiter=limiter), _oracle(orc, p, 120, limiter))
+
+
+def test_narrow_dd_kernel_walls_and_energy_flux_correction(orc, lbm):
+    """NEQ walls on x (moving, heated), equilibrium and zero-gradient y edges, Pr = 0.71, on a
+    grid of 10 rows."""
+    p = wl.shear_layer(96, ny=10)
+    p.bc = [(wl.BC_NEQ_WALL, 1.0, 0.0, 0.02, 1.01), (wl.BC_NEQ_WALL, 1.0, 0.0, -0.03, 0.99),
+            (wl.BC_EQUILIBRIUM, 1.02, 0.01, 0.0, 1.0), (wl.BC_ZERO_GRADIENT, 0, 0, 0, 0)]
+    _check(_run(lbm, p, 300, kernel=9), _oracle(orc, p, 300))
+
+
+@pytest.mark.parametrize("Pr", [0.5, 2.0])
+def test_narrow_dd_kernel_couette_channel(orc, lbm, Pr):
+    """A 24-cell Couette channel (walls at y) on narrow tiles, 1000 steps."""
+    p = wl.couette(Pr, nx=32, ny=24)
+    _check(_run(lbm, p, 1000, kernel=9), _oracle(orc, p, 1000))
+
+
+def test_narrow_dd_kernel_dy_not_dx(orc, lbm):
+    p = wl.shear_layer(100, ny=7)
+    p.dy = 1.6 * p.dx
+    _check(_run(lbm, p, 200, kernel=9), _oracle(orc, p, 200))
+
+
+def test_narrow_dd_kernel_sod_full_solve(orc, lbm):
+    """The 200 x 4 Sod tube, automatic float64 choice (narrow tiles), the full 2000-step solve."""
+    p = wl.sod(200, 4)
+    s = lbm.Solver.from_problem(p)
+    assert s.step_kernel == 9
+    s.init(*p.fields())
+    s.step(2000)
+    _check(s, _oracle(orc, p, 2000))
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_narrow_dd_kernel_matches_wide_tiles_and_plain(lbm, limiter):
+    """On a grid where both fit, narrow and 32 x 32 tiles give the same bits after 60 steps (the
+    same double-float operations on each value; the tiles only change where a value is staged),
+    and both match the float64 plain kernel to 1e-12."""
+    p = wl.shock_interface(nx=150, ny=70, steps=60)
+    a = _run(lbm, p, 60, kernel=9, limiter=limiter).get_state()
+    b = _run(lbm, p, 60, kernel=8, limiter=limiter).get_state()
+    c = _run(lbm, p, 60, kernel=1, limiter=limiter).get_state()
+    assert np.array_equal(a, b)
+    assert np.abs(a - c).max() <= 1e-12 * np.abs(c).max()
+
+
+def test_narrow_dd_kernel_rejected_where_it_does_not_fit(lbm):
+    for nx, ny in ((31, 16), (64, 3)):
+        p = wl.shear_layer(max(nx, ny), ny=ny)
+        p.nx = nx
+        p.rho, p.ux, p.uy, p.T = (np.ascontiguousarray(a[:, :nx]) for a in (p.rho, p.ux, p.uy, p.T))
+        with pytest.raises(lbm.LbmError):
+            lbm.Solver.from_problem(p, step_kernel=9)
