@@ -62,13 +62,13 @@ TRAFFIC_PER_CELL = {
             "sha": "3611ad9250829546"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "04e90657479a99f4"},
-    "dd": {"bytes": 248.04, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
-           "sha": "a2afc1f726475ef7"},
+    "dd": {"bytes": 247.89, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": "237e12bcaa275850"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
 # float64 kernel on 32 x 32 tiles, counted by ncu on the same sources
 # (profiles/k_step_dd_f64_shear_layer.md); None when the sources changed since.
-DD_FP32_OPS = {"ops": 3761.3, "sha": "a2afc1f726475ef7"}
+DD_FP32_OPS = {"ops": 3761.3, "sha": "237e12bcaa275850"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 
