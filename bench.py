@@ -62,13 +62,13 @@ TRAFFIC_PER_CELL = {
             "sha": "3611ad9250829546"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "04e90657479a99f4"},
-    "dd": {"bytes": 247.89, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
-           "sha": "237e12bcaa275850"},
+    "dd": {"bytes": 247.90, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": "b5db80af574dc01f"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
 # float64 kernel on 32 x 32 tiles, counted by ncu on the same sources
 # (profiles/k_step_dd_f64_shear_layer.md); None when the sources changed since.
-DD_FP32_OPS = {"ops": 3761.3, "sha": "237e12bcaa275850"}
+DD_FP32_OPS = {"ops": 3649.3, "sha": "b5db80af574dc01f"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 
@@ -541,19 +541,24 @@ def _pinned_fields(ny, nx, count):
 
 
 def timed_steps(lbm, s, steps, device):
-    """Device time of `steps` steps of one context (CUDA events on its stream) and the mean
-    duration of its fused-step and ghost launches (the library's own events)."""
+    """Device time of `steps` steps of one context (CUDA events on its stream, no per-step
+    instrumentation: on a small grid the library's per-launch events add about 9 us a step),
+    then the mean duration of its fused-step and ghost launches over `steps` more steps timed
+    with the library's own events."""
     import torch
     stream = torch.cuda.current_stream(device)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
-    lbm.lbm_profile_begin(s.h, steps)
     ev0.record(stream)
     s.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    lbm.lbm_profile_begin(s.h, steps)
+    s.step(steps)
+    torch.cuda.synchronize(device)
     prof = lbm.lbm_profile_end(s.h)
-    return ev0.elapsed_time(ev1), prof[0] / max(prof[1], 1), prof[2] / max(prof[3], 1)
+    return ms, prof[0] / max(prof[1], 1), prof[2] / max(prof[3], 1)
 
 
 def kernel_name(s, precision):

@@ -123,26 +123,30 @@ __device__ __forceinline__ dd recip(dd x)
 // far below the pair's own accuracy).
 __device__ __forceinline__ dd norm(dd a) { return fast2sum(a.hi, a.lo); }
 
-// Lexicographic order of normalised values (hi decides, lo breaks ties).
-__device__ __forceinline__ bool dd_lt(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-
 // Twice the MC slope, 2 minmod(2a, (a + b)/2, 2b) = sign(a) min(4|a|, 4|b|, |a + b|) when a and
 // b agree in sign and 0 otherwise (Sec. III, reading A6); as mc2 of lbm_device.cuh.  a and b
-// must be normalised (norm); their sum is renormalised here.  (Comparing the signed pairs with
-// the sign folded into the comparisons, instead of flipping all three to magnitudes, measured
-// 7% slower over the whole step.)
+// must be normalised (norm), so that their high parts carry their signs; they agree when
+// a.hi b.hi > 0 (a product below 2^-149 counts as disagreement: then the smaller difference
+// is below 2^-74, so the slope, at most 4 times it, is below 2^-72, far below the populations'
+// 2^-47 resolution, and is taken as 0).  Two
+// candidates x, y of the sign of a are ordered by the float32 value
+// (x.hi - y.hi) + (x.lo - y.lo), whose sign is that of x - y (zero only for x = y or x, y within
+// a few units of 2^-47 of each other, where either is the slope to the pairs' accuracy); the
+// smaller magnitude is the lower value for a > 0 and the higher for a < 0.  The sum a + b is
+// left unnormalised (its low part stays within a few units of its high part's last place,
+// which the ordering tolerates).  Three float32 operations and a predicate per comparison;
+// flipping the three pairs to magnitudes and comparing lexicographically took 4% more of the
+// step.
 __device__ __forceinline__ dd mc2n(dd a, dd b)
 {
-    const dd s = norm(a + b);
-    const unsigned sa = __float_as_uint(a.hi), sb = __float_as_uint(b.hi);
-    const bool agree = ((sa ^ sb) >> 31) == 0u && a.hi != 0.0f && b.hi != 0.0f;
-    // work on magnitudes: flip all three when a < 0 (then b, s < 0 as well)
-    const float sg = (sa >> 31) ? -1.0f : 1.0f;
-    const dd A = dd{a.hi * sg, a.lo * sg}, B = dd{b.hi * sg, b.lo * sg}, S = dd{s.hi * sg, s.lo * sg};
-    const dd m = dd_lt(A, B) ? A : B;
+    const dd s = a + b;
+    const bool agree = __fmul_rn(a.hi, b.hi) > 0.0f;
+    const bool neg = a.hi < 0.0f;
+    const float dab = __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+    const dd m = ((dab < 0.0f) != neg) ? a : b;
     const dd m4 = scale2(m, 4.0f);
-    const dd r = dd_lt(m4, S) ? m4 : S;
-    return agree ? dd{r.hi * sg, r.lo * sg} : dd{0.0f, 0.0f};
+    const float dms = __fadd_rn(__fsub_rn(m4.hi, s.hi), __fsub_rn(m4.lo, s.lo));
+    return agree ? (((dms < 0.0f) != neg) ? m4 : s) : dd{0.0f, 0.0f};
 }
 
 // As mc2n, for pairs not yet normalised.

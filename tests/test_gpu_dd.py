@@ -251,6 +251,9 @@ def test_narrow_dd_kernel_matches_wide_tiles_and_plain(lbm, limiter):
 
 
 def test_narrow_dd_kernel_rejected_where_it_does_not_fit(lbm):
+    """Narrow tiles need 32 columns and 4 rows; codes above 9 are unknown."""
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver.from_problem(wl.shear_layer(64, ny=32), step_kernel=10)
     for nx, ny in ((31, 16), (64, 3)):
         p = wl.shear_layer(max(nx, ny), ny=ny)
         p.nx = nx
