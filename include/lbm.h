@@ -155,7 +155,10 @@ int lbm_create_ex(int nx, int ny, double dx, double dt, double gamma, double Pr,
 int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *v, const double *T);
 
 /* Enqueue n >= 1 time steps (ghost fill + fused collide/convect per step; Eq. (3) and
-   the update of Sec. III).  Asynchronous on the context's stream.
+   the update of Sec. III).  Asynchronous on the context's stream.  Runs of 16 steps or more
+   (outside lbm_profile_begin / lbm_profile_end) replay pairs of steps from a CUDA graph that the
+   context captures on a private stream at first use, one per starting buffer (lbm_autotune
+   drops them): the same launches, one graph launch per pair.
    LBM_ERR_STATE if n <= 0 or the context was never initialised. */
 int lbm_step(lbm_ctx *ctx, int n);
 

@@ -54,6 +54,10 @@ struct lbm_ctx {
     CUtensorMap smap[2];          // row-copy descriptors (streaming kernel)
     CUtensorMap pmap[2];          // tile-copy descriptors of the double-buffered kernel
     CUtensorMap nmap[2];          // tile-copy descriptors of the narrow double-float tiles
+    // lbm_step replays pairs of steps (ghost fill + fused step, twice) from a CUDA graph per
+    // starting buffer, captured on a private stream at first use; lbm_autotune drops them
+    cudaGraphExec_t pair[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
     bool initialized = false;
     long long steps = 0;
     double dx = 0.0, dy = 0.0;
@@ -331,6 +335,38 @@ cudaError_t launch_fused_step(lbm_ctx *c, int in, cudaStream_t st)
     if (c->use_stream) return lbm::launch_step_stream(c->P, c->prec, &c->smap[in], c->f[in ^ 1], c->tma_err, st);
     if (c->use_tma) return lbm::launch_step_tma(c->P, c->prec, &c->tmap[in], c->f[in], c->f[in ^ 1], c->tma_err, st);
     return lbm::launch_step(c->P, c->prec, c->f[in], c->f[in ^ 1], st, c->plain_ty);
+}
+
+constexpr int kGraphSteps = 16;
+
+// The pair graph of context c starting from buffer `in` (two ghost fills and fused steps), captured
+// on the context's private stream at first use.
+cudaError_t step_pair_graph(lbm_ctx *c, int in)
+{
+    if (c->pair[in]) return cudaSuccess;
+    cudaError_t ce = c->cap ? cudaSuccess : cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ce;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < 2 && le == cudaSuccess; k++) {
+        le = lbm::launch_ghost(c->P, c->prec, c->f[in ^ k], c->cap, ghost_rows_only(c));
+        if (le == cudaSuccess) le = launch_fused_step(c, in ^ k, c->cap);
+    }
+    ce = cudaStreamEndCapture(c->cap, &graph);
+    if (ce == cudaSuccess) ce = le;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&c->pair[in], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) c->pair[in] = nullptr;
+    return ce;
+}
+
+void drop_step_graphs(lbm_ctx *c)
+{
+    for (cudaGraphExec_t &g : c->pair) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 }  // namespace
@@ -676,6 +712,18 @@ int lbm_step(lbm_ctx *c, int n)
     if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_state");
     cudaError_t ce = cudaSetDevice(c->device);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaSetDevice");
+    // runs of at least kGraphSteps steps outside profiling: pairs of steps from a graph (one
+    // launch instead of four; on small grids the launches, not the kernels, set the pace)
+    if (!c->prof && n >= kGraphSteps) {
+        ce = step_pair_graph(c, c->cur);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "step graph");
+        for (; n >= 2; n -= 2) {
+            ce = cudaGraphLaunch(c->pair[c->cur], c->stream);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "step graph launch");
+            c->steps += 2;
+        }
+        if (n == 0) return LBM_OK;
+    }
     for (int s = 0; s < n; s++) {
         cudaEvent_t *ev = nullptr;
         if (c->prof && c->prof_used < c->prof_max) ev = &c->prof_ev[4 * c->prof_used++];
@@ -1019,6 +1067,7 @@ int lbm_autotune(lbm_ctx *c, int reps, int *choice)
     c->use_tma = best_c == 2;
     c->use_stream = best_c == 5;
     c->use_pipe = best_c == 6;
+    drop_step_graphs(c);
     c->use_dd = best_c == 8;
     c->use_ddn = best_c == 9;
     c->plain_ty = best_c == 3 ? 4 : (best_c == 4 ? 16 : (best_c == 7 ? 2 : 8));
@@ -1394,6 +1443,8 @@ void lbm_destroy(lbm_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    drop_step_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->alloc.free) {
         if (c->aux) c->alloc.free(c->aux, c->aux_bytes, c->stream, c->alloc.user);
