@@ -1104,10 +1104,11 @@ struct lbm_batch {
         int4 *dT = nullptr;
         int ntiles = 0, max_ghost = 0;
         int nt = lbm::kBatchThreads;             // threads (= cells) per tile
-        // batched TMA-staged kernel: the members it serves (indices into members, in launch
-        // order) and their TileGrid blocks (Coef<float> or Coef<dd> by precision)
+        // batched TMA-staged kernels: the members they serve (indices into members, in launch
+        // order; float64 members on 32 x 32 tiles in tk, on narrow 32 x 4 tiles in tkn) and their
+        // TileGrid blocks (Coef<float> or Coef<dd> by precision), tk's first
         std::vector<int> tk;
-        std::vector<int> tkn;                    // float64 members on narrow 32 x 4 tiles
+        std::vector<int> tkn;
         void *tblock = nullptr;
         size_t tbytes = 0;
         int ntt = 0;                             // tiles per step
@@ -1116,8 +1117,7 @@ struct lbm_batch {
     std::vector<Group> groups;
     // contexts on the streaming or the double-buffered kernel with at least a quarter wave of
     // its work: their ghost cells come from their group's batched ghost launch, their step from
-    // that kernel, launched on kForks forked streams so that the grids' kernels overlap; their
-    // buffer parity at capture time
+    // that kernel, launched on kForks forked streams so that the grids' kernels overlap
     static constexpr int kForks = 8;
     std::vector<int> solo;
     std::vector<int> cap_cur;                   // every context's buffer parity at graph capture
