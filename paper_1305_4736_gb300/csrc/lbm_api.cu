@@ -1104,11 +1104,15 @@ struct lbm_batch {
         int4 *dT = nullptr;
         int ntiles = 0, max_ghost = 0;
         int nt = lbm::kBatchThreads;             // threads (= cells) per tile
-        // batched TMA-staged kernels: the members they serve (indices into members, in launch
-        // order; float64 members on 32 x 32 tiles in tk, on narrow 32 x 4 tiles in tkn) and their
-        // TileGrid blocks (Coef<float> or Coef<dd> by precision), tk's first
-        std::vector<int> tk;
-        std::vector<int> tkn;
+        // batched TMA-staged kernels: the row spans they serve (member index into members, first
+        // row, rows; in launch order; float64 spans on 32 x 32 tiles in tk, on narrow 32 x 4
+        // tiles in tkn) and one TileGrid block per span (Coef<float> or Coef<dd> by precision),
+        // tk's first.  A float64 member on 32 x 32 tiles whose last tile row would hold at most
+        // 24 of its rows has those rows in a narrow span.
+        struct Span {
+            int k, y0, rows;
+        };
+        std::vector<Span> tk, tkn;
         void *tblock = nullptr;
         size_t tbytes = 0;
         int ntt = 0;                             // tiles per step
@@ -1146,8 +1150,8 @@ cudaError_t batch_upload_cur(lbm_batch *b)
 // (float32 tile kernel, or float64 double-float kernel on 32 x 32 tiles) and, in float64, over
 // the members `tkn` on narrow 32 x 4 tiles, with every member's input map, output buffer and flag
 // resolved for this step's parity.  The group's TileGrid table holds tk's blocks, then tkn's.
-cudaError_t batch_launch_tma_list(lbm_batch *b, const lbm_batch::Group &g, const std::vector<int> &list, bool narrow,
-                                  const char *tg0, int phase, cudaStream_t st)
+cudaError_t batch_launch_tma_list(lbm_batch *b, const lbm_batch::Group &g, const std::vector<lbm_batch::Group::Span> &list,
+                                  bool narrow, const char *tg0, int phase, cudaStream_t st)
 {
     static thread_local lbm::TmaBatchArgs A;
     const bool f64 = g.prec == LBM_FP64;
@@ -1157,14 +1161,16 @@ cudaError_t batch_launch_tma_list(lbm_batch *b, const lbm_batch::Group &g, const
         const int n = (int)std::min<size_t>(lbm::kTmaBatchGrids, list.size() - c0);
         int tiles = 0;
         for (int k = 0; k < n; k++) {
-            const lbm_ctx *c = b->ctxs[g.members[list[c0 + k]]];
+            const lbm_batch::Group::Span &sp = list[c0 + k];
+            const lbm_ctx *c = b->ctxs[g.members[sp.k]];
             const int in = c->cur ^ phase;
             A.map[k] = narrow ? c->nmap[in] : c->tmap[in];
             A.out[k] = c->f[in ^ 1];
             A.err[k] = c->tma_err;
             A.first[k] = tiles;
             A.ntx[k] = (c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX;
-            tiles += A.ntx[k] * ((c->P.ny + tr - 1) / tr);
+            A.y0[k] = sp.y0;
+            tiles += A.ntx[k] * ((sp.rows + tr - 1) / tr);
         }
         A.first[n] = tiles;
         A.n = n;
@@ -1263,10 +1269,14 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
     // a float64 member on narrow double-float tiles whose grid takes 32 x 32 tiles steps on those
     // in the batch (the same bits: the two shapes run the same operations on every value; spread
     // over a batch, the larger tiles cost less per cell)
-    std::vector<char> wide(n, 0);
+    std::vector<char> wide(n, 0), split(n, 0);
     for (int i = 0; i < n; i++) {
         lbm_ctx *c = ctxs[i];
         wide[i] = c->use_dd || (c->use_ddn && lbm::tma_supported(c->P, LBM_FP64) && make_tile_maps(c));
+        // a last 32 x 32 tile row with at most 24 of the grid's rows: those rows on narrow tiles
+        // (a narrow tile costs about 1.3x per cell, a part-filled row of 32 x 32 tiles 32 / rows)
+        const int rem = c->P.ny % lbm::TmaShape<double>::TR;
+        split[i] = wide[i] && rem > 0 && rem <= 24 && lbm::dd_narrow_supported(c->P) && make_narrow_maps(c);
     }
     cudaGetLastError();
     for (int i = 0; i < n; i++) {
@@ -1308,17 +1318,28 @@ int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out)
             g.hG.push_back(lbm::BatchGrid{{c->f[0], c->f[1]}, c->tma_err, c->cur, 0});
             g.max_ghost = std::max(g.max_ghost, 4 * (c->P.nx + c->P.ny));
             if (g.tma[k]) {
-                const bool narrow = g.prec == LBM_FP64 && !wide[g.members[k]];
-                const int trk = narrow ? lbm::DdNarrowShape::TR : tr;
-                (narrow ? g.tkn : g.tk).push_back((int)k);
-                g.ntt += ((c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX) * ((c->P.ny + trk - 1) / trk);
-                if (g.prec == LBM_FP64)
-                    (narrow ? htdn : htd)
-                        .push_back(lbm::TileGrid<lbm::Coef<lbm::dd>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
-                                                                     c->P.plane, 0, c->cdd});
-                else
-                    htf.push_back(lbm::TileGrid<lbm::Coef<float>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
-                                                                  c->P.plane, 0, c->P.cf});
+                const int i = g.members[k], ntx = (c->P.nx + lbm::kTmaTX - 1) / lbm::kTmaTX;
+                if (g.prec == LBM_FP64) {
+                    const lbm::TileGrid<lbm::Coef<lbm::dd>> blk{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
+                                                                c->P.plane, 0, c->cdd};
+                    const int nr = lbm::DdNarrowShape::TR;
+                    const int wide_rows = !wide[i] ? 0 : (split[i] ? c->P.ny - c->P.ny % tr : c->P.ny);
+                    if (wide_rows > 0) {
+                        g.tk.push_back({(int)k, 0, wide_rows});
+                        g.ntt += ntx * ((wide_rows + tr - 1) / tr);
+                        htd.push_back(blk);
+                    }
+                    if (wide_rows < c->P.ny) {
+                        g.tkn.push_back({(int)k, wide_rows, c->P.ny - wide_rows});
+                        g.ntt += ntx * ((c->P.ny - wide_rows + nr - 1) / nr);
+                        htdn.push_back(blk);
+                    }
+                    continue;
+                }
+                g.tk.push_back({(int)k, 0, c->P.ny});
+                g.ntt += ntx * ((c->P.ny + tr - 1) / tr);
+                htf.push_back(lbm::TileGrid<lbm::Coef<float>>{c->P.nx, c->P.ny, c->P.pitch, c->P.has_c9,
+                                                              c->P.plane, 0, c->P.cf});
                 continue;
             }
             if (g.own[k]) continue;                  // ghost cells only

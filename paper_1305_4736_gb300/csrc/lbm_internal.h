@@ -99,7 +99,7 @@ struct DdNarrowShape {
 bool dd_narrow_supported(const Params &P);
 // Batched TMA-staged steps over the tiles of up to kTmaBatchGrids grids of a batch group, one
 // CTA per tile of kTmaTX x TmaShape<R>::TR cells: grid k owns the launch's tiles first[k] ..
-// first[k+1] - 1, row by row, ntx[k] to a row.  A CTA finds its grid and tile from blockIdx
+// first[k+1] - 1, row by row from row y0[k], ntx[k] to a row.  A CTA finds its grid and tile from blockIdx
 // and this parameter block alone, so that its tile copy is issued before any load from global
 // memory; the host resolves each grid's input map, output buffer and error flag for the
 // launch's buffer parity.  float32 (the tile kernel) and float64 in double-float arithmetic.
@@ -110,6 +110,7 @@ struct TmaBatchArgs {
     int *err[kTmaBatchGrids];           // grid k's copy-wait flag
     int first[kTmaBatchGrids + 1];      // first[n] = tiles of the launch
     int ntx[kTmaBatchGrids];            // tiles per row of grid k
+    int y0[kTmaBatchGrids];             // first row of grid k's tiles in this launch
     int n;                              // grids of the launch
 };
 // Per-grid block of a batched launch (global memory, one per grid in launch order): the

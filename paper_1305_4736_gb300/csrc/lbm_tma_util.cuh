@@ -102,7 +102,8 @@ __device__ __noinline__ void wrap_halo(const Params &P, const R *__restrict__ fi
 // constants differ, so their convection runs as one float2 per pair.
 
 // Batched launches: the grid of tile b (the largest k with first[k] <= b, a binary search on
-// the parameter block, uniform across the CTA) and the tile's origin.
+// the parameter block, uniform across the CTA) and the tile's origin (grid k's tiles start at
+// row y0[k]).
 __device__ __forceinline__ int batch_tile(const TmaBatchArgs &A, int b, int tr, int &x0, int &y0)
 {
     int lo = 0, hi = A.n - 1;
@@ -114,7 +115,7 @@ __device__ __forceinline__ int batch_tile(const TmaBatchArgs &A, int b, int tr, 
     const int local = b - A.first[lo], nt = A.ntx[lo];
     const int ty = local / nt;
     x0 = (local - ty * nt) * kTmaTX;
-    y0 = ty * tr;
+    y0 = A.y0[lo] + ty * tr;
     return lo;
 }
 
