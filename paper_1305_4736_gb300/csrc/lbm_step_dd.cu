@@ -273,8 +273,9 @@ __device__ __forceinline__ void dd_tile(const PP &P, const Coef<dd> &C, unsigned
                         if (lane == 0) Sl = eS;
                         tx = D + C.hh[shell] * (Sx - Sl);
                     } else {
-                        // moving left: d1 = -D(x+1), slopes -S(x) and -S(x+1) (mc2 is odd and
-                        // symmetric)
+                        // moving left: d1 = -D(x+1), slopes -S(x) and -S(x+1) (mc2n is odd and
+                        // symmetric, up to the choice between candidates within 2^-47 of each
+                        // other)
                         dd Sr = shfl_down_dd(Sx);
                         if (lane == kTmaTX - 1) Sr = eS;
                         tx = (-Dr) + C.hh[shell] * ((-Sx) - (-Sr));
