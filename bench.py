@@ -58,17 +58,17 @@ TOTALS_EVERY = 100
 # of the kernel sources it was captured from.  bench reports the traffic only while the sources
 # still hash to that value, else null.
 TRAFFIC_PER_CELL = {
-    "f32": {"bytes": 125.88, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
-            "sha": "3611ad9250829546"},
+    "f32": {"bytes": 125.89, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "07a62d28b685263d"},
     "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "04e90657479a99f4"},
-    "dd": {"bytes": 247.90, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
-           "sha": "b5db80af574dc01f"},
+    "dd": {"bytes": 247.87, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
+           "sha": "a502465f89b98477"},
 }
 # float32-pipe operations (add, multiply, FMA: one each) per cell of one launch of the double-float
 # float64 kernel on 32 x 32 tiles, counted by ncu on the same sources
 # (profiles/k_step_dd_f64_shear_layer.md); None when the sources changed since.
-DD_FP32_OPS = {"ops": 3649.3, "sha": "b5db80af574dc01f"}
+DD_FP32_OPS = {"ops": 3649.3, "sha": "a502465f89b98477"}
 FP32_LANES_PER_SM = 128           # float32 FMA lanes per SM per cycle (GB300)
 
 
