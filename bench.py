@@ -60,8 +60,8 @@ TOTALS_EVERY = 100
 TRAFFIC_PER_CELL = {
     "f32": {"bytes": 125.89, "sources": ("lbm_step_tma.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
             "sha": "07a62d28b685263d"},
-    "f64": {"bytes": 251.43, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
-            "sha": "04e90657479a99f4"},
+    "f64": {"bytes": 251.63, "sources": ("lbm_step_stream.cu", "lbm_device.cuh", "lbm_tma_util.cuh"),
+            "sha": "01bf052590e27491"},
     "dd": {"bytes": 247.87, "sources": ("lbm_step_dd.cu", "lbm_dd.cuh", "lbm_device.cuh", "lbm_tma_util.cuh"),
            "sha": "a502465f89b98477"},
 }
