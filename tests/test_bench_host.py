@@ -52,3 +52,22 @@ def test_reduce_max_over_two_gloo_ranks():
         p.join(120)
     res = sorted(q.get(timeout=10) for _ in range(2))
     assert res == [(0, 11.0), (1, 11.0)]
+
+
+def test_traffic_and_op_counts_keyed_to_their_kernels_and_sources(monkeypatch):
+    """The ncu-derived DRAM traffic and float32-op counts apply only to the kernel they were
+    captured from, and only while its sources hash to the captured value."""
+    cells = 1 << 20
+    for mode, name in (("f32", "k_step_tma<float,dev,MC>"), ("dd", bench.KERNEL_NAMES[8]),
+                       ("f64", "k_step_stream<double,plain,MC>")):
+        t = bench.TRAFFIC_PER_CELL[mode]
+        assert bench.kernel_sources_sha(t["sources"]) == t["sha"], mode   # captured from these sources
+        assert bench.traffic_per_launch(mode, cells, name) == pytest.approx(t["bytes"] * cells)
+    # other kernels of the same precision get no traffic figure
+    assert bench.traffic_per_launch("dd", cells, bench.KERNEL_NAMES[9]) is None
+    assert bench.traffic_per_launch("f32", cells, "k_step<float,dev,MC,256>") is None
+    assert bench.dd_fp32_ops_per_cell() == bench.DD_FP32_OPS["ops"]
+    # a source change voids both
+    monkeypatch.setattr(bench, "kernel_sources_sha", lambda names: "0" * 16)
+    assert bench.traffic_per_launch("dd", cells, bench.KERNEL_NAMES[8]) is None
+    assert bench.dd_fp32_ops_per_cell() is None
